@@ -1,0 +1,484 @@
+"""FP64 CPU oracle for the frequency-domain FWI misfit and adjoint-state gradient.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously-correct
+statement of what the GPU library computes.  Only the test suite, the smoke
+check and the benchmark's CPU-baseline leg may import it; the product path
+never does, and it shares no code with the CUDA sources.
+
+What it follows (Da Silva & Herrmann, "A Unified 2D/3D Large Scale Software
+Environment for Nonlinear Inverse Problems"):
+  * Sec. 2, eq. (helmholtz) and the extended-domain system: the Helmholtz
+    operator (d~x^2 + d~y^2 + d~z^2 + w^2 m) with d~x = (1/eta(x)) dx inside the
+    damping layer, zero Dirichlet on the outer boundary, m extended into the
+    layer by copying in the normal direction;
+  * Sec. 2, eq. (mainprob): f(m) = sum_{s,w} 1/2 || P_r H_w(m)^{-1} q_{s,w} - d_{s,w} ||^2;
+  * Appendix A, eqs. (dU2), (dH), (dHadj): T dm = w^2 diag(u) dm with A = I,
+    T* = w^2 diag(conj u), v = -H^{-H} P_r^T (P_r u - d), grad f = sum Re(T* v);
+  * Table derivstuff / Listing pdefunc: the summation over sources and
+    frequencies of Re(T(U)^H V), mapped back to the physical grid by the
+    adjoint of the extension (to_phys);
+  * Sec. 4 (Alg. vcycle text): linear-interpolation prolongation and its
+    adjoint as restriction (transfer operators only).
+
+Readings taken where the paper is silent (each also listed in the design doc):
+  * m = 1/v^2 and H = L_eta + w^2 diag(m);
+  * eta_d(x) = 1 + i sigma_d(x)/w with sigma = sigma_max (dist/W)^2, W the
+    layer width on that side, sigma_max = 3 v_ref ln(1000) / (2 npml h);
+  * the stretched second derivative is discretised as
+    a_i [ b_{i+1/2}(u_{i+1}-u_i) - b_{i-1/2}(u_i-u_{i-1}) ] / h^2 with
+    a = 1/eta at nodes and b = 1/eta at half nodes (so A = I in eq. (dH));
+  * sources and receivers sit on grid nodes: the windowed-sinc operators of
+    Sec. 3 reduce to point sampling; a unit source is 1/h^dim at its node;
+  * extra high-side layer cells ("pad") make (N+1) divisible by 2^(levels-1)
+    for vertex-centred coarsening.
+
+Every array here is complex128 / float64.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+# ---------------------------------------------------------------------------
+# Grid and damping layer (Sec. 2, extended domain Omega' of Omega)
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Grid:
+    """Computational grid: the physical box plus damping layers on every side.
+
+    n    = (nx, ny, nz) physical nodes; 2D uses ny = 1 and npml[1] = 0.
+    npml = layer cells per side; pad = extra cells on the high side."""
+    dim: int
+    n: tuple
+    h: float
+    npml: tuple
+    pad: tuple
+    v_ref: float
+    sigma_max: tuple  # per axis
+
+    @property
+    def N(self):
+        return tuple(self.n[d] + 2 * self.npml[d] + self.pad[d] for d in range(3))
+
+    @property
+    def shape(self):
+        """Array shape (Nz, Ny, Nx) of a computational-grid field."""
+        Nx, Ny, Nz = self.N
+        return (Nz, Ny, Nx)
+
+    @property
+    def size(self):
+        Nx, Ny, Nz = self.N
+        return Nx * Ny * Nz
+
+    @property
+    def phys_shape(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx)
+
+    @property
+    def n_phys(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+
+def make_grid(dim: int, n: Sequence[int], h: float, npml: Sequence[int], v_ref: float,
+              levels: int = 1, sigma_max: Optional[Sequence[float]] = None) -> Grid:
+    """Build the extended grid.  With `levels` > 1 the high side receives extra
+    layer cells so that N_d + 1 is divisible by 2^(levels-1) on every active axis."""
+    n = tuple(int(v) for v in n)
+    npml = tuple(int(v) for v in npml)
+    if dim == 2:
+        assert n[1] == 1 and npml[1] == 0
+    q = 1 << max(levels - 1, 0)
+    pad = []
+    for d in range(3):
+        if dim == 2 and d == 1:
+            pad.append(0)
+            continue
+        base = n[d] + 2 * npml[d]
+        pad.append((-(base + 1)) % q)
+    if sigma_max is None:
+        sigma_max = tuple((3.0 * v_ref * np.log(1000.0) / (2.0 * npml[d] * h)) if npml[d] > 0 else 0.0
+                          for d in range(3))
+    return Grid(dim=dim, n=n, h=float(h), npml=npml, pad=tuple(pad), v_ref=float(v_ref),
+                sigma_max=tuple(float(s) for s in sigma_max))
+
+
+def sigma_at(t: np.ndarray, d: int, g: Grid) -> np.ndarray:
+    """Damping sigma_d at computational-grid coordinate t (in cells, may be
+    half-integer) along axis d.  Zero inside the physical box; quadratic in the
+    distance to the box across the layer of that side."""
+    lo = g.npml[d]
+    hi = g.npml[d] + g.n[d] - 1
+    W_lo = g.npml[d] * g.h
+    W_hi = (g.npml[d] + g.pad[d]) * g.h
+    t = np.asarray(t, dtype=np.float64)
+    s = np.zeros_like(t)
+    if g.npml[d] == 0 and g.pad[d] == 0:
+        return s
+    below = t < lo
+    above = t > hi
+    if W_lo > 0:
+        s[below] = g.sigma_max[d] * (((lo - t[below]) * g.h) / W_lo) ** 2
+    if W_hi > 0:
+        s[above] = g.sigma_max[d] * (((t[above] - hi) * g.h) / W_hi) ** 2
+    return s
+
+
+def axis_coefficients(g: Grid, d: int, omega: float):
+    """1D stretched second-derivative coefficients along axis d.
+
+    Returns (cm, cp, cd): for node i, (L_d u)_i = cm[i] u_{i-1} + cd[i] u_i + cp[i] u_{i+1}
+    with cm = a_i b_{i-1/2} / h^2, cp = a_i b_{i+1/2} / h^2, cd = -(cm + cp),
+    a = 1/eta at nodes, b = 1/eta at half nodes, eta = 1 + i sigma / omega."""
+    N = g.N[d]
+    i = np.arange(N, dtype=np.float64)
+    a = 1.0 / (1.0 + 1j * sigma_at(i, d, g) / omega)
+    b_minus = 1.0 / (1.0 + 1j * sigma_at(i - 0.5, d, g) / omega)
+    b_plus = 1.0 / (1.0 + 1j * sigma_at(i + 0.5, d, g) / omega)
+    h2 = g.h * g.h
+    cm = a * b_minus / h2
+    cp = a * b_plus / h2
+    return cm, cp, -(cm + cp)
+
+
+def second_difference_1d(cm, cp, cd) -> sp.csr_matrix:
+    """Tridiagonal 1D matrix with zero Dirichlet values beyond both ends."""
+    N = len(cd)
+    return sp.diags([cm[1:], cd, cp[:-1]], offsets=[-1, 0, 1], shape=(N, N), format="csr",
+                    dtype=np.complex128)
+
+
+def helmholtz_matrix(g: Grid, m_comp: np.ndarray, omega: float) -> sp.csr_matrix:
+    """H(m, omega) = sum_d L_d + omega^2 diag(m) on the computational grid.
+
+    Linear index p = ix + Nx*(iy + Ny*iz), so the x operator acts on the
+    fastest Kronecker factor."""
+    Nx, Ny, Nz = g.N
+    Ix, Iy, Iz = (sp.identity(k, dtype=np.complex128, format="csr") for k in (Nx, Ny, Nz))
+    Lx = second_difference_1d(*axis_coefficients(g, 0, omega))
+    Lz = second_difference_1d(*axis_coefficients(g, 2, omega))
+    H = sp.kron(Iz, sp.kron(Iy, Lx)) + sp.kron(Lz, sp.kron(Iy, Ix))
+    if g.dim == 3:
+        Ly = second_difference_1d(*axis_coefficients(g, 1, omega))
+        H = H + sp.kron(Iz, sp.kron(Ly, Ix))
+    H = H + sp.diags(omega * omega * np.asarray(m_comp, dtype=np.float64).ravel())
+    return sp.csr_matrix(H)
+
+
+# ---------------------------------------------------------------------------
+# Model extension E and its adjoint (Sec. 2; Listing pdefunc "to_phys")
+# ---------------------------------------------------------------------------
+
+def _phys_of_comp(g: Grid, d: int) -> np.ndarray:
+    """For each computational node along axis d, the physical node it copies."""
+    return np.clip(np.arange(g.N[d]) - g.npml[d], 0, g.n[d] - 1)
+
+
+def extend(g: Grid, m_phys: np.ndarray) -> np.ndarray:
+    """E m: copy the physical model into the layers along the normal direction."""
+    m = np.asarray(m_phys, dtype=np.float64).reshape(g.phys_shape)
+    ix, iy, iz = (_phys_of_comp(g, d) for d in range(3))
+    return m[np.ix_(iz, iy, ix)]
+
+
+def extend_adjoint(g: Grid, g_comp: np.ndarray) -> np.ndarray:
+    """E^T g: sum each computational value onto the physical node it was copied from."""
+    gc = np.asarray(g_comp, dtype=np.float64).reshape(g.shape)
+    ix, iy, iz = (_phys_of_comp(g, d) for d in range(3))
+    out = np.zeros(g.phys_shape)
+    np.add.at(out, np.ix_(iz, iy, ix), gc)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Sources, receivers (Sec. 2, P_r and the localised q; Listing pdefunc Ps, Pr)
+# ---------------------------------------------------------------------------
+
+def comp_index(g: Grid, phys_idx: np.ndarray) -> np.ndarray:
+    """Computational linear index of a physical linear node index."""
+    nx, ny, _ = g.n
+    Nx, Ny, _ = g.N
+    p = np.asarray(phys_idx, dtype=np.int64)
+    ix = p % nx
+    iy = (p // nx) % ny
+    iz = p // (nx * ny)
+    return (ix + g.npml[0]) + Nx * ((iy + g.npml[1]) + Ny * (iz + g.npml[2]))
+
+
+def source_fields(g: Grid, src_idx, Q, weight: complex = 1.0) -> np.ndarray:
+    """q_s = weight * sum_k Q[k, s] delta_h(x - x_k), delta_h = 1/h^dim at the node.
+    Returns (nsrc, size)."""
+    Q = np.asarray(Q, dtype=np.complex128)
+    nsrc = Q.shape[1]
+    q = np.zeros((nsrc, g.size), dtype=np.complex128)
+    ci = comp_index(g, src_idx)
+    for s in range(nsrc):
+        np.add.at(q[s], ci, weight * Q[:, s] / g.h ** g.dim)
+    return q
+
+
+def sample_receivers(g: Grid, u: np.ndarray, rec_idx) -> np.ndarray:
+    """P_r u for fields of shape (..., size)."""
+    return np.asarray(u)[..., comp_index(g, rec_idx)]
+
+
+def spread_receivers(g: Grid, r: np.ndarray, rec_idx) -> np.ndarray:
+    """P_r^T r: place receiver values back on their nodes (zero elsewhere)."""
+    r = np.asarray(r, dtype=np.complex128)
+    out = np.zeros(r.shape[:-1] + (g.size,), dtype=np.complex128)
+    ci = comp_index(g, rec_idx)
+    flat = out.reshape(-1, g.size)
+    rr = r.reshape(-1, r.shape[-1])
+    for k in range(flat.shape[0]):
+        np.add.at(flat[k], ci, rr[k])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Linear solvers: sparse direct, and restarted GMRES (Saad & Schultz 1986)
+# ---------------------------------------------------------------------------
+
+class DirectSolver:
+    """Sparse LU of H, factorised once and reused across right-hand sides
+    (the 2D strategy of Sec. 3)."""
+
+    def __init__(self, H: sp.spmatrix):
+        self.H = sp.csc_matrix(H)
+        self.lu = spla.splu(self.H)
+
+    def solve(self, b: np.ndarray) -> np.ndarray:
+        return self.lu.solve(np.asarray(b, dtype=np.complex128))
+
+    def solve_adjoint(self, b: np.ndarray) -> np.ndarray:
+        return self.lu.solve(np.asarray(b, dtype=np.complex128), trans="H")
+
+
+def gmres(A, b: np.ndarray, tol: float = 1e-13, restart: int = 60, maxiter: int = 100000,
+          x0: Optional[np.ndarray] = None):
+    """Restarted GMRES without preconditioning.
+
+    Arnoldi with modified Gram-Schmidt (one re-orthogonalisation pass), the
+    Hessenberg least-squares problem reduced by Givens rotations, restart
+    after `restart` steps.  Stops when the true residual ||b - A x|| <= tol ||b||.
+    Returns (x, total_iterations, relative_residual)."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0
+    it = 0
+    r = b - A @ x
+    beta = np.linalg.norm(r)
+    while it < maxiter:
+        if beta <= tol * bnorm:
+            break
+        V = np.zeros((restart + 1, b.size), dtype=np.complex128)
+        Hh = np.zeros((restart + 1, restart), dtype=np.complex128)
+        cs = np.zeros(restart, dtype=np.complex128)
+        sn = np.zeros(restart, dtype=np.complex128)
+        e = np.zeros(restart + 1, dtype=np.complex128)
+        e[0] = beta
+        V[0] = r / beta
+        k_used = 0
+        for j in range(restart):
+            w = A @ V[j]
+            for _pass in range(2):
+                for i in range(j + 1):
+                    hij = np.vdot(V[i], w)
+                    Hh[i, j] += hij
+                    w = w - hij * V[i]
+            Hh[j + 1, j] = np.linalg.norm(w)
+            if Hh[j + 1, j] != 0:
+                V[j + 1] = w / Hh[j + 1, j]
+            # apply previous rotations to the new column
+            for i in range(j):
+                t = cs[i] * Hh[i, j] + sn[i] * Hh[i + 1, j]
+                Hh[i + 1, j] = -np.conj(sn[i]) * Hh[i, j] + np.conj(cs[i]) * Hh[i + 1, j]
+                Hh[i, j] = t
+            # new rotation zeroing Hh[j+1, j]
+            a_, b_ = Hh[j, j], Hh[j + 1, j]
+            rr = np.hypot(abs(a_), abs(b_))
+            if rr == 0:
+                cs[j], sn[j] = 1.0, 0.0
+            else:
+                cs[j] = a_ / rr
+                sn[j] = b_ / rr
+                # rotation G = [[conj(c), conj(s)], [-s, c]] maps (a, b) -> (rr, 0)
+                cs[j] = np.conj(cs[j])
+                sn[j] = np.conj(sn[j])
+            Hh[j, j] = cs[j] * a_ + sn[j] * b_
+            Hh[j + 1, j] = 0.0
+            e[j + 1] = -np.conj(sn[j]) * e[j]
+            e[j] = cs[j] * e[j]
+            it += 1
+            k_used = j + 1
+            if abs(e[j + 1]) <= 0.5 * tol * bnorm or it >= maxiter:
+                break
+        y = np.linalg.solve(np.triu(Hh[:k_used, :k_used]), e[:k_used])
+        x = x + V[:k_used].T @ y
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+    return x, it, beta / bnorm
+
+
+class GmresSolver:
+    """H^{-1} and H^{-H} by restarted GMRES on the explicit sparse matrix."""
+
+    def __init__(self, H: sp.spmatrix, tol: float = 1e-13, restart: int = 60,
+                 maxiter: int = 200000):
+        self.H = sp.csr_matrix(H)
+        self.HH = sp.csr_matrix(self.H.conj().T)
+        self.tol, self.restart, self.maxiter = tol, restart, maxiter
+        self.iterations = []
+
+    def solve(self, b):
+        x, it, _ = gmres(self.H, b, self.tol, self.restart, self.maxiter)
+        self.iterations.append(it)
+        return x
+
+    def solve_adjoint(self, b):
+        x, it, _ = gmres(self.HH, b, self.tol, self.restart, self.maxiter)
+        self.iterations.append(it)
+        return x
+
+
+def make_solver(H, kind: str = "direct", **kw):
+    if kind == "direct":
+        return DirectSolver(H)
+    if kind == "gmres":
+        return GmresSolver(H, **kw)
+    raise ValueError(kind)
+
+
+# ---------------------------------------------------------------------------
+# The three calls: forward modelling, adjoint solve, misfit + gradient
+# ---------------------------------------------------------------------------
+
+def _omega(f_hz: float) -> float:
+    return 2.0 * np.pi * float(f_hz)
+
+
+def forward(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, wavelet=None,
+            solver: str = "direct", want_fields: bool = True, **solver_kw):
+    """FORW_MODEL of Listing pdefunc: U = H^{-1} Q per frequency, D = P_r U.
+    Returns (U [nfreq, nsrc, size] or None, D [nfreq, nsrc, nrec])."""
+    mc = extend(g, m_phys)
+    Qa = np.asarray(Q)
+    nf, ns, nr = len(freqs_hz), Qa.shape[1], len(rec_idx)
+    U = np.zeros((nf, ns, g.size), dtype=np.complex128) if want_fields else None
+    D = np.zeros((nf, ns, nr), dtype=np.complex128)
+    for k, fr in enumerate(freqs_hz):
+        w = 1.0 if wavelet is None else wavelet[k]
+        S = make_solver(helmholtz_matrix(g, mc, _omega(fr)), solver, **solver_kw)
+        q = source_fields(g, src_idx, Qa, w)
+        for s in range(ns):
+            u = S.solve(q[s])
+            if want_fields:
+                U[k, s] = u
+            D[k, s] = sample_receivers(g, u, rec_idx)
+    return U, D
+
+
+def adjoint(g: Grid, m_phys, freqs_hz, rec_idx, R_in, solver: str = "direct", **solver_kw):
+    """V = H^{-H} P_r^T R per frequency and source.  Returns [nfreq, nsrc, size]."""
+    mc = extend(g, m_phys)
+    R_in = np.asarray(R_in, dtype=np.complex128)
+    nf, ns = R_in.shape[0], R_in.shape[1]
+    V = np.zeros((nf, ns, g.size), dtype=np.complex128)
+    for k, fr in enumerate(freqs_hz):
+        S = make_solver(helmholtz_matrix(g, mc, _omega(fr)), solver, **solver_kw)
+        b = spread_receivers(g, R_in[k], rec_idx)
+        for s in range(ns):
+            V[k, s] = S.solve_adjoint(b[s])
+    return V
+
+
+def misfit_and_gradient(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None,
+                        mask=None, solver: str = "direct", return_fields: bool = False,
+                        **solver_kw):
+    """OBJ of Listing pdefunc with the least-squares misfit (Sec. 2):
+
+        u   = H^{-1} q                     (state)
+        r   = P_r u - d                    (grad of phi = 1/2 ||.||^2)
+        f  += 1/2 ||r||^2
+        v   = H^{-H} (-P_r^T r)            (adjoint state, Table derivstuff V(m))
+        g  += Re( T(u)^* v ) = w^2 Re(conj(u) v)     (eq. (dHadj) with A = I)
+
+    summed over frequencies and sources (optionally masked), then mapped to the
+    physical grid by E^T.  Returns (f, g_phys[, U, V])."""
+    mc = extend(g, m_phys)
+    Qa = np.asarray(Q)
+    d_obs = np.asarray(d_obs, dtype=np.complex128)
+    nf, ns = len(freqs_hz), Qa.shape[1]
+    f = 0.0
+    gc = np.zeros(g.size)
+    U = np.zeros((nf, ns, g.size), dtype=np.complex128) if return_fields else None
+    V = np.zeros((nf, ns, g.size), dtype=np.complex128) if return_fields else None
+    for k, fr in enumerate(freqs_hz):
+        om = _omega(fr)
+        w = 1.0 if wavelet is None else wavelet[k]
+        S = make_solver(helmholtz_matrix(g, mc, om), solver, **solver_kw)
+        q = source_fields(g, src_idx, Qa, w)
+        for s in range(ns):
+            if mask is not None and not mask[k][s]:
+                continue
+            u = S.solve(q[s])
+            r = sample_receivers(g, u, rec_idx) - d_obs[k, s]
+            f += 0.5 * float(np.vdot(r, r).real)
+            v = S.solve_adjoint(-spread_receivers(g, r, rec_idx))
+            gc += om * om * np.real(np.conj(u) * v)
+            if return_fields:
+                U[k, s], V[k, s] = u, v
+    gp = extend_adjoint(g, gc)
+    if return_fields:
+        return f, gp, U, V
+    return f, gp
+
+
+def misfit(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, mask=None,
+           solver: str = "direct", **solver_kw) -> float:
+    """f(m) alone (one PDE solve per source and frequency, Table derivcosts)."""
+    _, D = forward(g, m_phys, freqs_hz, src_idx, Q, rec_idx, wavelet, solver, want_fields=False,
+                   **solver_kw)
+    r = D - np.asarray(d_obs)
+    if mask is not None:
+        r = r * np.asarray(mask, dtype=np.float64)[..., None]
+    return 0.5 * float(np.vdot(r, r).real)
+
+
+# ---------------------------------------------------------------------------
+# Inter-grid transfers of the V-cycle (Sec. 4): linear interpolation P and
+# restriction R = 2^-dim P^T (full weighting)
+# ---------------------------------------------------------------------------
+
+def prolong_1d_matrix(Nc: int) -> sp.csr_matrix:
+    """Linear interpolation from Nc coarse to 2*Nc+1 fine nodes, zero beyond the
+    walls: fine 2j+1 = coarse j; fine 2j = (coarse j-1 + coarse j)/2."""
+    Nf = 2 * Nc + 1
+    rows, cols, vals = [], [], []
+    for j in range(Nc):
+        rows += [2 * j + 1, 2 * j, 2 * j + 2]
+        cols += [j, j, j]
+        vals += [1.0, 0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(Nf, Nc))
+
+
+def prolongation(fine_N: Sequence[int], dim: int) -> sp.csr_matrix:
+    """Tensor-product (bi/tri)linear interpolation for fine sizes (Nx, Ny, Nz)."""
+    Nx, Ny, Nz = fine_N
+    Px = prolong_1d_matrix((Nx - 1) // 2)
+    Pz = prolong_1d_matrix((Nz - 1) // 2)
+    Py = prolong_1d_matrix((Ny - 1) // 2) if dim == 3 else sp.identity(Ny, format="csr")
+    return sp.csr_matrix(sp.kron(Pz, sp.kron(Py, Px)))
+
+
+def restriction(fine_N: Sequence[int], dim: int) -> sp.csr_matrix:
+    """R = 2^-dim P^T."""
+    return sp.csr_matrix(prolongation(fine_N, dim).T) * (0.5 ** dim)
