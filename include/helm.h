@@ -1,0 +1,210 @@
+/*
+ * helm.h -- C ABI of the GB300 frequency-domain FWI library.
+ *
+ * The library evaluates the reduced least-squares objective of the paper
+ * (Da Silva & Herrmann, "A Unified 2D/3D Large Scale Software Environment for
+ * Nonlinear Inverse Problems", Sec. 2, eq. (mainprob))
+ *
+ *     f(m) = sum_{w} sum_{s} 1/2 || P_r H_w(m)^{-1} q_{s,w} - d_{s,w} ||^2
+ *
+ * and its adjoint-state gradient (Appendix A, eqs. (dU2), (dH), (dHadj);
+ * Table derivstuff; Listing pdefunc, OBJ branch)
+ *
+ *     u = H^{-1} q,   v = -H^{-H} P_r^T (P_r u - d),   g = E^T sum w^2 Re(conj(u) v),
+ *
+ * where H(m,w) = Lap_eta + w^2 diag(m) is the 7-point (5-point in 2D) finite-
+ * difference Helmholtz operator of Sec. 2 (eq. (helmholtz) on the extended
+ * domain with damping layers), m = 1/v^2, and E copies the physical model
+ * into the layers along the normal direction (its adjoint E^T sums back).
+ * Solves are matrix-free: restarted FGMRES (Sec. 4) with the multi-level
+ * ML-GMRES preconditioner of Sec. 4 (Alg. vcycle; Fig. mlgmres) or damped
+ * Jacobi, in FP64 or with complex64 inner solves under FP64 iterative
+ * refinement.
+ *
+ * Conventions for every call
+ *  - Bulk arrays are DEVICE pointers owned by the caller; the library never
+ *    allocates, frees or keeps them.  Scalars, option structs, frequency lists
+ *    and report arrays are HOST memory.
+ *  - Complex values are interleaved (re, im): complex128 = two doubles,
+ *    complex64 = two floats.
+ *  - Grid fields are x-fastest: physical [nz][ny][nx] (n_phys values) and
+ *    computational [Nz][Ny][Nx] (n_comp values, layers included).  2D uses
+ *    ny = 1.  Node indices are PHYSICAL linear indices ix + nx*(iy + ny*iz).
+ *  - Multi-field arrays are [nfreq][nsrc][...] (frequency slowest).
+ *  - `workspace` is caller-allocated device scratch of at least the size that
+ *    helm_workspace_size() reports for the same call and sizes, 256-byte aligned.
+ *  - Calls are enqueued on `stream` but BLOCK the host: the solvers read
+ *    per-RHS convergence state between restart cycles, so every output is
+ *    complete when a call returns.  Calls on one plan must not overlap.
+ *  - Return value: HELM_OK or a negative helm_status.  HELM_E_NOCONV still
+ *    writes every output; the per-RHS reports say which solves fell short.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t-compatible handle (NULL = the legacy default stream). */
+typedef struct CUstream_st* helm_stream_t;
+
+typedef enum {
+  HELM_OK = 0,
+  HELM_E_INVAL = -1,     /* bad sizes, options, pointers or node indices */
+  HELM_E_NOMEM = -2,     /* workspace smaller than helm_workspace_size() */
+  HELM_E_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+  HELM_E_NOCONV = -4,    /* some solve missed its tolerance (outputs written) */
+  HELM_E_NONFINITE = -5, /* NaN/Inf met in a residual */
+  HELM_E_TIMEOUT = -6    /* reserved: a bounded device wait expired */
+} helm_status;
+
+typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
+typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGMRES = 2 } helm_precond;
+typedef enum {
+  HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3
+} helm_call;
+
+/* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
+ * of Sec. 3 carries the layer width).  The damping profile is
+ * sigma(x) = sigma_max (dist(x)/W)^2 across a layer of width W, and the
+ * stretched derivative is (1/eta) d/dx with eta = 1 + i sigma / w. */
+typedef struct {
+  int dim;               /* 2 or 3 */
+  int n[3];              /* physical nodes along x, y, z (dim 2: n[1] = 1) */
+  double h;              /* node spacing [m] */
+  int npml[3];           /* damping-layer cells on each side (dim 2: npml[1] = 0) */
+  double v_ref;          /* velocity [m/s] setting the default sigma_max */
+  double sigma_max[3];   /* 0 selects 3 v_ref ln(1000) / (2 npml h) */
+  int levels;            /* 1..3 grid levels; with levels > 1 extra high-side layer
+                            cells make N_d + 1 divisible by 2^(levels-1) */
+} helm_grid;
+
+/* Solver options ("LinSolveOpts" of Sec. 3; ML-GMRES parameters
+ * (k_so, k_si, k_co, k_ci) of Sec. 4). */
+typedef struct {
+  int precision;         /* helm_precision */
+  int precond;           /* helm_precond */
+  int k_inner;           /* Krylov length of one outer FGMRES restart cycle (1..32) */
+  int max_cycles;        /* outer restart cycles per solve (per refinement step) */
+  double tol;            /* target ||q - H u|| / ||q||, checked in FP64 */
+  double tol_inner;      /* MIXED: residual reduction asked of each complex64 solve */
+  int max_refine;        /* MIXED: iterative-refinement steps */
+  int k_so, k_si;        /* ML-GMRES smoother GMRES: cycles, Krylov length */
+  int k_co, k_ci;        /* ML-GMRES coarse FGMRES: cycles, Krylov length */
+  double jacobi_omega;   /* damped-Jacobi weight */
+  int jacobi_sweeps;     /* damped-Jacobi sweeps per preconditioner application */
+  int max_batch;         /* right-hand sides solved together (0 = all at once) */
+} helm_solve_opts;
+
+/* One report per right-hand side (frequency-major, like the fields). */
+typedef struct {
+  int status;            /* HELM_OK, HELM_E_NOCONV or HELM_E_NONFINITE */
+  int iters;             /* outer Krylov iterations summed over refinement steps */
+  int refinements;       /* MIXED: refinement steps taken (FP64: 1) */
+  double rel_resid;      /* final ||q - H u|| / ||q|| in FP64 */
+} helm_rhs_report;
+
+typedef struct helm_plan helm_plan;
+
+/* Fill `opts` with the defaults: MIXED, ML-GMRES (3,5,3,5), FGMRES(5),
+ * tol 1e-10, tol_inner 1e-4.  Returns HELM_OK. */
+int helm_default_opts(helm_solve_opts* opts);
+
+/* Validate `grid` and `opts` and build a host-side plan (no device memory).
+ * HELM_E_INVAL on a bad field; *plan is NULL then. */
+int helm_plan_create(const helm_grid* grid, const helm_solve_opts* opts, helm_plan** plan);
+void helm_plan_destroy(helm_plan* plan);
+
+/* Computational sizes N[3] (layers and padding included), n_comp = N0*N1*N2
+ * and n_phys = n0*n1*n2. */
+int helm_plan_dims(const helm_plan* plan, int N[3], size_t* n_comp, size_t* n_phys);
+
+/* Device workspace in bytes needed by `call` for the given sizes
+ * (n_rhs = nfreq*nsrc fields; nrec receivers). */
+int helm_workspace_size(const helm_plan* plan, int call, int nfreq, int nsrc, int nrec,
+                        size_t* bytes);
+
+/* y = H(m, w) x, or y = H(m, w)^H x when `adjoint` != 0, for `nrhs` fields on
+ * the computational grid sharing m and w = 2 pi freq_hz (Sec. 2 operator; its
+ * adjoint is the conjugate transpose, Sec. 5.1 adjoint test).  precision
+ * HELM_FP64: x, y complex128; HELM_MIXED: x, y complex64 (FP32 arithmetic).
+ * m_phys: float64 [n_phys].  x and y must not overlap. */
+int helm_apply(helm_plan* plan, const double* m_phys, double freq_hz, int adjoint, int precision,
+               const void* x, void* y, int nrhs, void* workspace, size_t ws_bytes,
+               helm_stream_t stream);
+
+/* Forward modelling (Listing pdefunc, FORW_MODEL): for every frequency k and
+ * source s solve H(m, w_k) u = q with q = wavelet[k] sum_j Q[j, s] delta_h(x - x_j),
+ * delta_h = 1/h^dim at the node src_idx[j], then D = P_r u (u sampled at rec_idx).
+ *   m_phys   float64 [n_phys]
+ *   freqs_hz HOST float64 [nfreq]
+ *   src_idx  int32 [n_srcloc]; Q complex128 [n_srcloc][nsrc]
+ *   wavelet  complex128 [nfreq] or NULL (all ones)
+ *   rec_idx  int32 [nrec]
+ *   U_out    complex128 [nfreq][nsrc][n_comp] or NULL
+ *   D_out    complex128 [nfreq][nsrc][nrec] or NULL
+ *   reports  HOST [nfreq*nsrc] or NULL */
+int helm_forward(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                 const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc,
+                 const void* wavelet, const int32_t* rec_idx, int nrec,
+                 void* U_out, void* D_out, void* workspace, size_t ws_bytes,
+                 helm_rhs_report* reports, helm_stream_t stream);
+
+/* Adjoint solve: V = H(m, w_k)^{-H} P_r^T R for every frequency and source
+ * (the adjoint wavefield of Table derivstuff without its minus sign).
+ *   R_in  complex128 [nfreq][nsrc][nrec];  V_out complex128 [nfreq][nsrc][n_comp] */
+int helm_adjoint(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                 const int32_t* rec_idx, int nrec, const void* R_in, int nsrc, void* V_out,
+                 void* workspace, size_t ws_bytes, helm_rhs_report* reports,
+                 helm_stream_t stream);
+
+/* Misfit and gradient (Sec. 2 eq. (mainprob); Appendix A; Listing pdefunc OBJ):
+ *   f = sum_{k,s} 1/2 ||P_r u_{k,s} - d_{k,s}||^2,
+ *   g = E^T sum_{k,s} w_k^2 Re(conj(u_{k,s}) v_{k,s}),  v = -H^{-H} P_r^T (P_r u - d),
+ * over the (k, s) pairs whose mask byte is non-zero (all when mask is NULL; the
+ * paper's batch-mode source/frequency subsets, Sec. 3).
+ *   d_obs   complex128 [nfreq][nsrc][nrec]
+ *   mask    uint8 [nfreq][nsrc] or NULL
+ *   f_out   float64 [1];  g_out float64 [n_phys] (overwritten) */
+int misfit_and_gradient(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                        const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc,
+                        const void* wavelet, const int32_t* rec_idx, int nrec,
+                        const void* d_obs, const uint8_t* mask, double* f_out, double* g_out,
+                        void* workspace, size_t ws_bytes, helm_rhs_report* reports,
+                        helm_stream_t stream);
+
+/* Static description of a status code. */
+const char* helm_status_string(int status);
+
+/* Number of kernels this library launched since the process started (a
+ * monotonically increasing host counter). */
+uint64_t helm_kernel_launch_count(void);
+
+/* Instrumentation (no counterpart in the paper): per-kernel-class timing.
+ * While enabled, every launch of a class is bracketed by CUDA events on its
+ * own stream and the algorithmic bytes it moves (inputs read once, outputs
+ * written once) are summed.  helm_profile_enable(on) clears the counters and
+ * switches recording on or off; helm_profile_read() waits for the recorded
+ * events and returns launches, summed device milliseconds and bytes. */
+typedef enum {
+  HELM_PROF_STENCIL_C64 = 0,  /* stencil / residual, complex64 */
+  HELM_PROF_STENCIL_C128 = 1, /* stencil / residual, complex128 */
+  HELM_PROF_KRYLOV_C64 = 2,   /* fused Gram-Schmidt / norm / update passes, complex64 */
+  HELM_PROF_KRYLOV_C128 = 3,  /* the same in complex128 */
+  HELM_PROF_SMALL = 4,        /* per-right-hand-side reductions and Hessenberg updates */
+  HELM_PROF_TRANSFER = 5,     /* restriction / prolongation */
+  HELM_PROF_FWI = 6,          /* sources, receivers, misfit, gradient, extension */
+  HELM_PROF_MISC = 7,         /* conversions, zero fills, Jacobi */
+  HELM_PROF_NCLASS = 8
+} helm_prof_class;
+int helm_profile_enable(int on);
+int helm_profile_read(int cls, uint64_t* launches, double* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

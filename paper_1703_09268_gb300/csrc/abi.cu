@@ -1,0 +1,461 @@
+// The extern "C" entry points of include/helm.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "solver.h"
+
+namespace helm {
+
+std::atomic<uint64_t> g_launches{0};
+
+// ---------------------------------------------------------------------------
+// Per-class launch timing
+// ---------------------------------------------------------------------------
+namespace {
+struct ProfRec {
+  int cls;
+  double bytes;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<cudaEvent_t> g_ev_pool;
+std::vector<ProfRec> g_recs;
+uint64_t g_prof_n[PC_COUNT];
+double g_prof_ms[PC_COUNT];
+double g_prof_bytes[PC_COUNT];
+
+cudaEvent_t take_event() {
+  if (!g_ev_pool.empty()) {
+    cudaEvent_t e = g_ev_pool.back();
+    g_ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void drain_records() {
+  for (ProfRec& r : g_recs) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    g_prof_n[r.cls] += 1;
+    g_prof_ms[r.cls] += ms;
+    g_prof_bytes[r.cls] += r.bytes;
+    g_ev_pool.push_back(r.a);
+    g_ev_pool.push_back(r.b);
+  }
+  g_recs.clear();
+}
+}  // namespace
+
+ProfScope::ProfScope(int c, double by, cudaStream_t s) : cls(c), bytes(by), st(s), slot(-1) {
+  if (!g_prof_on) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (g_recs.size() >= 200000) drain_records();
+  ProfRec r{c, by, take_event(), take_event()};
+  cudaEventRecord(r.a, st);
+  g_recs.push_back(r);
+  slot = (int)g_recs.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < (int)g_recs.size()) cudaEventRecord(g_recs[slot].b, st);
+}
+
+// ---------------------------------------------------------------------------
+// Plan construction
+// ---------------------------------------------------------------------------
+static int build_plan(const helm_grid* g, const helm_solve_opts* o, helm_plan* P) {
+  if (!g || !o) return HELM_E_INVAL;
+  if (g->dim != 2 && g->dim != 3) return HELM_E_INVAL;
+  if (!(g->h > 0.0) || !std::isfinite(g->h)) return HELM_E_INVAL;
+  if (g->levels < 1 || g->levels > MAX_LEVELS) return HELM_E_INVAL;
+  for (int d = 0; d < 3; ++d) {
+    if (g->npml[d] < 0 || g->n[d] < 1) return HELM_E_INVAL;
+    if (g->sigma_max[d] < 0.0 || !std::isfinite(g->sigma_max[d])) return HELM_E_INVAL;
+  }
+  if (g->dim == 2 && (g->n[1] != 1 || g->npml[1] != 0)) return HELM_E_INVAL;
+  const int active[3] = {1, g->dim == 3 ? 1 : 0, 1};
+  for (int d = 0; d < 3; ++d)
+    if (active[d] && g->n[d] < 2) return HELM_E_INVAL;
+  bool need_vref = false;
+  for (int d = 0; d < 3; ++d)
+    if (g->npml[d] > 0 && g->sigma_max[d] == 0.0) need_vref = true;
+  if (need_vref && !(g->v_ref > 0.0)) return HELM_E_INVAL;
+  // options
+  if (o->precision != HELM_FP64 && o->precision != HELM_MIXED) return HELM_E_INVAL;
+  if (o->precond < HELM_PRECOND_NONE || o->precond > HELM_PRECOND_MLGMRES) return HELM_E_INVAL;
+  if (o->k_inner < 1 || o->k_inner > KMAX || o->max_cycles < 1) return HELM_E_INVAL;
+  if (!(o->tol > 0.0) || !(o->tol < 1.0)) return HELM_E_INVAL;
+  if (o->precision == HELM_MIXED && (!(o->tol_inner > 0.0) || !(o->tol_inner < 1.0) || o->max_refine < 1))
+    return HELM_E_INVAL;
+  if (o->precond == HELM_PRECOND_MLGMRES) {
+    if (o->k_so < 1 || o->k_si < 1 || o->k_si > KMAX || o->k_co < 1 || o->k_ci < 1 || o->k_ci > KMAX)
+      return HELM_E_INVAL;
+    if (g->levels < 2) return HELM_E_INVAL;
+  }
+  if (o->precond == HELM_PRECOND_JACOBI && (!(o->jacobi_omega > 0.0) || o->jacobi_sweeps < 1))
+    return HELM_E_INVAL;
+  if (o->max_batch < 0) return HELM_E_INVAL;
+
+  std::memset(P, 0, sizeof(*P));
+  P->g = *g;
+  P->o = *o;
+  P->L = o->precond == HELM_PRECOND_MLGMRES ? g->levels : 1;
+  const int q = 1 << (g->levels - 1);
+  for (int d = 0; d < 3; ++d) {
+    if (!active[d]) {
+      P->pad[d] = 0;
+    } else {
+      const int base = g->n[d] + 2 * g->npml[d];
+      P->pad[d] = ((-(base + 1)) % q + q) % q;
+    }
+    if (g->sigma_max[d] > 0.0)
+      P->smax[d] = g->sigma_max[d];
+    else
+      P->smax[d] = g->npml[d] > 0 ? 3.0 * g->v_ref * std::log(1000.0) / (2.0 * g->npml[d] * g->h) : 0.0;
+  }
+  P->n_phys = (size_t)g->n[0] * g->n[1] * g->n[2];
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    LevelGeom& L = P->lev[l];
+    for (int d = 0; d < 3; ++d) {
+      if (l == 0)
+        L.N[d] = active[d] ? g->n[d] + 2 * g->npml[d] + P->pad[d] : 1;
+      else
+        L.N[d] = active[d] ? (P->lev[l - 1].N[d] - 1) / 2 : 1;
+    }
+    if (g->dim == 3) {
+      L.K[0] = L.N[0]; L.K[1] = L.N[1]; L.K[2] = L.N[2];
+    } else {
+      L.K[0] = L.N[0]; L.K[1] = L.N[2]; L.K[2] = 1;
+    }
+    L.n = (size_t)L.N[0] * L.N[1] * L.N[2];
+    L.Nmax = std::max(L.K[0], std::max(L.K[1], L.K[2]));
+    L.h = g->h * (double)(1 << l);
+    if (l < P->L)
+      for (int d = 0; d < 3; ++d)
+        if (active[d] && L.N[d] < 3) return HELM_E_INVAL;
+  }
+  return HELM_OK;
+}
+
+static bool aligned256(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+// Bind a workspace to a Ctx after checking its size.
+static int bind(helm_plan* P, int call, int nfreq, int nsrc, int nrec, void* ws, size_t ws_bytes,
+                helm_stream_t stream, Ctx& c) {
+  const size_t need = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
+  if (!ws || ws_bytes < need) return HELM_E_NOMEM;
+  if (!aligned256(ws)) return HELM_E_INVAL;
+  layout(*P, call, nfreq, nsrc, nrec, (char*)ws, &c);
+  c.st = (cudaStream_t)stream;
+  return HELM_OK;
+}
+
+static int read_err(Ctx& c, int* h) {
+  cudaMemcpyAsync(h, c.err, 4 * sizeof(int), cudaMemcpyDeviceToHost, c.st);
+  return sync_check(c);
+}
+
+static void fill_reports(helm_rhs_report* reports, const std::vector<int>& g,
+                         const std::vector<SlotReport>& rep) {
+  if (!reports) return;
+  for (size_t a = 0; a < g.size(); ++a) {
+    helm_rhs_report& r = reports[g[a]];
+    r.status = rep[a].status;
+    r.iters = rep[a].iters;
+    r.refinements = rep[a].refine;
+    r.rel_resid = rep[a].rel;
+  }
+}
+
+static int worst(int a, int b) {
+  if (a == HELM_E_CUDA || b == HELM_E_CUDA) return HELM_E_CUDA;
+  if (a == HELM_E_NONFINITE || b == HELM_E_NONFINITE) return HELM_E_NONFINITE;
+  if (a == HELM_E_NOCONV || b == HELM_E_NOCONV) return HELM_E_NOCONV;
+  return a != HELM_OK ? a : b;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" {
+
+int helm_default_opts(helm_solve_opts* o) {
+  if (!o) return HELM_E_INVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HELM_MIXED;
+  o->precond = HELM_PRECOND_MLGMRES;
+  o->k_inner = 5;
+  o->max_cycles = 200;
+  o->tol = 1e-10;
+  o->tol_inner = 1e-4;
+  o->max_refine = 12;
+  o->k_so = 3;
+  o->k_si = 5;
+  o->k_co = 3;
+  o->k_ci = 5;
+  o->jacobi_omega = 0.6;
+  o->jacobi_sweeps = 1;
+  o->max_batch = 0;
+  return HELM_OK;
+}
+
+int helm_plan_create(const helm_grid* grid, const helm_solve_opts* opts, helm_plan** plan) {
+  if (!plan) return HELM_E_INVAL;
+  *plan = nullptr;
+  helm_plan* P = new (std::nothrow) helm_plan;
+  if (!P) return HELM_E_NOMEM;
+  const int st = build_plan(grid, opts, P);
+  if (st != HELM_OK) {
+    delete P;
+    return st;
+  }
+  *plan = P;
+  return HELM_OK;
+}
+
+void helm_plan_destroy(helm_plan* plan) { delete plan; }
+
+int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys) {
+  if (!P) return HELM_E_INVAL;
+  if (N)
+    for (int d = 0; d < 3; ++d) N[d] = P->lev[0].N[d];
+  if (n_comp) *n_comp = P->lev[0].n;
+  if (n_phys) *n_phys = P->n_phys;
+  return HELM_OK;
+}
+
+int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
+  if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_MISFIT_GRAD) return HELM_E_INVAL;
+  *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
+  return HELM_OK;
+}
+
+int helm_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, int precision,
+               const void* x, void* y, int nrhs, void* ws, size_t ws_bytes, helm_stream_t stream) {
+  if (!P || !m_phys || !x || !y || nrhs < 1 || !(freq_hz > 0.0) || !std::isfinite(freq_hz))
+    return HELM_E_INVAL;
+  if (precision != HELM_FP64 && precision != HELM_MIXED) return HELM_E_INVAL;
+  Ctx c;
+  int st = bind(P, HELM_CALL_APPLY, 1, nrhs, 0, ws, ws_bytes, stream, c);
+  if (st != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, &freq_hz)) != HELM_OK) return st;
+  std::vector<int> g(nrhs);
+  for (int i = 0; i < nrhs; ++i) g[i] = i;
+  if ((st = set_batch(c, g)) != HELM_OK) return st;
+  const int dir = adjoint ? 1 : 0;
+  if (precision == HELM_FP64) {
+    launch_stencil<double>(op_view<double>(c, 0, dir), c.slot_f, c.act, c.na, (const double2*)x,
+                           Scale<double>{}, nullptr, Scale<double>{}, (double2*)y, c.st);
+  } else {
+    launch_stencil<float>(op_view<float>(c, 0, dir), c.slot_f, c.act, c.na, (const float2*)x,
+                          Scale<float>{}, nullptr, Scale<float>{}, (float2*)y, c.st);
+  }
+  return sync_check(c);
+}
+
+static int check_common(helm_plan* P, const double* m_phys, const double* freqs, int nfreq, int nsrc) {
+  if (!P || !m_phys || !freqs || nfreq < 1 || nsrc < 1) return HELM_E_INVAL;
+  for (int k = 0; k < nfreq; ++k)
+    if (!(freqs[k] > 0.0) || !std::isfinite(freqs[k])) return HELM_E_INVAL;
+  return HELM_OK;
+}
+
+static int check_indices(Ctx& c, const int32_t* src, int nsrcloc, const int32_t* rec, int nrec) {
+  if (src) launch_check_idx(*c.P, src, nsrcloc, c.err, c.st);
+  if (rec) launch_check_idx(*c.P, rec, nrec, c.err, c.st);
+  int h[4] = {0, 0, 0, 0};
+  if (read_err(c, h) != HELM_OK) return HELM_E_CUDA;
+  return h[0] == 0 ? HELM_OK : HELM_E_INVAL;
+}
+
+int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
+                 const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                 const int32_t* rec_idx, int nrec, void* U_out, void* D_out, void* ws, size_t ws_bytes,
+                 helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!src_idx || n_srcloc < 1 || !Q || nrec < 0 || (nrec > 0 && !rec_idx)) return HELM_E_INVAL;
+  if (D_out && nrec < 1) return HELM_E_INVAL;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_FORWARD, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, src_idx, n_srcloc, nrec > 0 ? rec_idx : nullptr, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  int result = HELM_OK;
+  for (int start = 0; start < nrhs; start += c.B) {
+    const int nb = std::min(c.B, nrhs - start);
+    std::vector<int> g(nb);
+    for (int a = 0; a < nb; ++a) g[a] = start + a;
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, (const double2*)wavelet, c.slot_f,
+                   c.slot_s, nb, c.q, c.err + 1, c.st);
+    std::vector<SlotReport> rep;
+    st = solve_batch(c, 0, c.q, c.u, nb, rep);
+    if (st == HELM_E_CUDA) return st;
+    result = worst(result, st);
+    for (auto& r : rep) result = worst(result, r.status);
+    if (U_out) launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
+    if (D_out) launch_receivers(*P, c.u, rec_idx, nrec, c.slot_g, nb, (double2*)D_out, nrec, c.st);
+    fill_reports(reports, g, rep);
+  }
+  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  return result;
+}
+
+int helm_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
+                 const int32_t* rec_idx, int nrec, const void* R_in, int nsrc, void* V_out, void* ws,
+                 size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!rec_idx || nrec < 1 || !R_in || !V_out) return HELM_E_INVAL;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_ADJOINT, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, nullptr, 0, rec_idx, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  int result = HELM_OK;
+  for (int start = 0; start < nrhs; start += c.B) {
+    const int nb = std::min(c.B, nrhs - start);
+    std::vector<int> g(nb);
+    for (int a = 0; a < nb; ++a) g[a] = start + a;
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_spread(*P, (const double2*)R_in, nrec, rec_idx, nrec, 1.0, c.slot_g, nb, c.q, c.st);
+    std::vector<SlotReport> rep;
+    st = solve_batch(c, 1, c.q, c.v, nb, rep);
+    if (st == HELM_E_CUDA) return st;
+    result = worst(result, st);
+    for (auto& r : rep) result = worst(result, r.status);
+    launch_copy_fields(c.v, (double2*)V_out, c.ident, nb, c.slot_g, n, c.st);
+    fill_reports(reports, g, rep);
+  }
+  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  return result;
+}
+
+int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
+                        const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                        const int32_t* rec_idx, int nrec, const void* d_obs, const uint8_t* mask,
+                        double* f_out, double* g_out, void* ws, size_t ws_bytes, helm_rhs_report* reports,
+                        helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out || !g_out)
+    return HELM_E_INVAL;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_MISFIT_GRAD, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, src_idx, n_srcloc, rec_idx, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  // (k, s) pairs to evaluate
+  std::vector<int> todo;
+  if (mask) {
+    std::vector<uint8_t> mh(nrhs);
+    cudaMemcpyAsync(mh.data(), mask, nrhs, cudaMemcpyDeviceToHost, c.st);
+    if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+    for (int i = 0; i < nrhs; ++i)
+      if (mh[i]) todo.push_back(i);
+  } else {
+    for (int i = 0; i < nrhs; ++i) todo.push_back(i);
+  }
+  if (reports)
+    for (int i = 0; i < nrhs; ++i) reports[i] = helm_rhs_report{HELM_OK, 0, 0, 0.0};
+  cudaMemsetAsync(c.gcomp, 0, sizeof(double) * n, c.st);
+  cudaMemsetAsync(f_out, 0, sizeof(double), c.st);
+  int result = HELM_OK;
+  for (size_t start = 0; start < todo.size(); start += c.B) {
+    const int nb = (int)std::min<size_t>(c.B, todo.size() - start);
+    std::vector<int> g(todo.begin() + start, todo.begin() + start + nb);
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    // state: u = H^{-1} q
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, (const double2*)wavelet, c.slot_f,
+                   c.slot_s, nb, c.q, c.err + 1, c.st);
+    std::vector<SlotReport> rf, ra;
+    st = solve_batch(c, 0, c.q, c.u, nb, rf);
+    if (st == HELM_E_CUDA) return st;
+    result = worst(result, st);
+    // misfit and adjoint source -P_r^T (P_r u - d)
+    launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.slot_f, c.slot_s, nsrc, c.ident,
+                           nb, c.res, c.f_slot, c.st);
+    launch_sum_f(c.f_slot, c.ident, nb, f_out, 1, c.st);
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_spread(*P, c.res, nrec, rec_idx, nrec, -1.0, c.ident, nb, c.q, c.st);
+    // adjoint state v = H^{-H} b
+    st = solve_batch(c, 1, c.q, c.v, nb, ra);
+    if (st == HELM_E_CUDA) return st;
+    result = worst(result, st);
+    // g += w^2 Re(conj(u) v)
+    launch_grad_accum(c.u, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    for (int a = 0; a < nb; ++a) {
+      SlotReport r = rf[a];
+      r.iters += ra[a].iters;
+      r.refine += ra[a].refine;
+      r.rel = std::max(rf[a].rel, ra[a].rel);
+      r.status = worst(rf[a].status, ra[a].status);
+      result = worst(result, r.status);
+      rf[a] = r;
+    }
+    fill_reports(reports, g, rf);
+  }
+  launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
+  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  return result;
+}
+
+const char* helm_status_string(int s) {
+  switch (s) {
+    case HELM_OK: return "ok";
+    case HELM_E_INVAL: return "invalid argument";
+    case HELM_E_NOMEM: return "workspace too small";
+    case HELM_E_CUDA: return "CUDA error";
+    case HELM_E_NOCONV: return "solve did not reach its tolerance";
+    case HELM_E_NONFINITE: return "non-finite residual";
+    case HELM_E_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+uint64_t helm_kernel_launch_count(void) { return g_launches.load(); }
+
+int helm_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  drain_records();
+  for (int i = 0; i < PC_COUNT; ++i) {
+    g_prof_n[i] = 0;
+    g_prof_ms[i] = 0.0;
+    g_prof_bytes[i] = 0.0;
+  }
+  g_prof_on = on != 0;
+  return HELM_OK;
+}
+
+int helm_profile_read(int cls, uint64_t* launches, double* ms, double* bytes) {
+  if (cls < 0 || cls >= PC_COUNT) return HELM_E_INVAL;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  drain_records();
+  if (launches) *launches = g_prof_n[cls];
+  if (ms) *ms = g_prof_ms[cls];
+  if (bytes) *bytes = g_prof_bytes[cls];
+  return HELM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Host-side solver orchestration and workspace layout (internal).
+#pragma once
+
+#include <functional>
+#include <vector>
+
+#include "common.cuh"
+
+namespace helm {
+
+// Sub-allocates the caller's workspace; with base == nullptr it only sizes.
+struct Bump {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T> T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+template <typename R> struct KInst {
+  int level = 0;
+  int k = 0;
+  bool flex = false;
+  cplx<R>* V = nullptr;  // (k+1) sets of B fields
+  cplx<R>* Z = nullptr;  // k sets (flexible only)
+  cplx<R>* w = nullptr;  // 1 set
+  KState ks{};
+};
+
+template <typename R> struct Hierarchy {
+  KInst<R> inst[MAX_KINST];
+  cplx<R>* r[MAX_LEVELS] = {};   // V-cycle residual per level
+  cplx<R>* b[MAX_LEVELS] = {};   // restricted right-hand side per level
+  cplx<R>* x[MAX_LEVELS] = {};   // coarse solution per level
+};
+
+// Everything one call needs on the device.
+struct Ctx {
+  const helm_plan* P = nullptr;
+  cudaStream_t st = nullptr;
+  int call = 0;
+  int nfreq = 0, nsrc = 0, nrec = 0;
+  int B = 0;      // slots per batch
+  int dir = 0;    // 0: H, 1: H^H
+  bool mixed = false;
+  // model and tables per level
+  double* m64[MAX_LEVELS] = {};
+  float* m32[MAX_LEVELS] = {};
+  double2* tab64[MAX_LEVELS][2] = {};
+  float2* tab32[MAX_LEVELS][2] = {};
+  double* omega = nullptr;
+  double* w2_64 = nullptr;
+  float* w2_32 = nullptr;
+  // slots
+  int* slot_f = nullptr;
+  int* slot_s = nullptr;
+  int* slot_g = nullptr;   // global (k, s) index of each slot
+  int* act = nullptr;      // device active list
+  int* ident = nullptr;    // 0..B-1
+  int* err = nullptr;      // [4] device error counters
+  double* partial = nullptr;
+  // FP64 fields
+  double2* q = nullptr;    // right-hand side
+  double2* u = nullptr;    // solution (forward field)
+  double2* v = nullptr;    // adjoint field
+  double2* r64 = nullptr;  // refinement residual
+  float2* b32 = nullptr;   // complex64 inner right-hand side r/||r||
+  float2* x32 = nullptr;   // complex64 inner solution
+  double* nrm = nullptr;   // [B] residual norms
+  double* qn = nullptr;    // [B] right-hand side norms
+  double2* res = nullptr;  // [B][nrec] receiver residuals
+  double* f_slot = nullptr;
+  double* gcomp = nullptr;
+  // Krylov hierarchies
+  Hierarchy<float> h32;
+  Hierarchy<double> h64;
+  KState ks64{};           // FP64 bookkeeping for refinement norms
+  // host state
+  std::vector<int> act_h;
+  int na = 0;
+};
+
+size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char* base, Ctx* c);
+
+// Per-slot outcome of one batched solve.
+struct SlotReport {
+  int status = HELM_OK;
+  int iters = 0;
+  int refine = 0;
+  double rel = 0.0;
+};
+
+// One-time per-call device setup: extended model on every level, tables, w^2.
+int setup_operator(Ctx& c, const double* m_phys, const double* freqs_hz);
+// Set the current batch: slots 0..nb-1 take global (k, s) indices g[0..nb-1].
+int set_batch(Ctx& c, const std::vector<int>& g);
+void set_active(Ctx& c, const std::vector<int>& a);
+// Solve H u = q (dir 0) or H^H u = q (dir 1) for all slots of the batch;
+// q and u are FP64 batch arrays.  Fills rep[0..nb-1].
+int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep);
+int sync_check(Ctx& c);
+
+template <typename R> OpView<R> op_view(const Ctx& c, int level, int dir);
+
+}  // namespace helm

@@ -1,0 +1,334 @@
+"""ctypes binding of the C ABI in include/helm.h (argument marshalling only).
+
+Every numerical step runs in libhelm.so's CUDA kernels; this module only
+checks tensor types, hands device pointers and the current CUDA stream to
+the library and allocates the caller-owned workspace with torch.  Importing
+it loads the library and raises if it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhelm.so")
+
+HELM_OK, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_CUDA, HELM_E_NOCONV, HELM_E_NONFINITE, HELM_E_TIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
+CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD = 0, 1, 2, 3
+PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
+                "misc"]
+
+
+class HelmGrid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double),
+                ("npml", ctypes.c_int * 3), ("v_ref", ctypes.c_double),
+                ("sigma_max", ctypes.c_double * 3), ("levels", ctypes.c_int)]
+
+
+class HelmSolveOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("k_inner", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double), ("tol_inner", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("k_so", ctypes.c_int), ("k_si", ctypes.c_int),
+                ("k_co", ctypes.c_int), ("k_ci", ctypes.c_int), ("jacobi_omega", ctypes.c_double),
+                ("jacobi_sweeps", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class HelmRhsReport(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("rel_resid", ctypes.c_double)]
+
+
+EXPORTS = ["helm_default_opts", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
+           "helm_workspace_size", "helm_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
+           "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read"]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhelm.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.helm_default_opts.argtypes = [ctypes.POINTER(HelmSolveOpts)]
+    lib.helm_plan_create.argtypes = [ctypes.POINTER(HelmGrid), ctypes.POINTER(HelmSolveOpts),
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    lib.helm_plan_destroy.argtypes = [P]
+    lib.helm_plan_destroy.restype = None
+    lib.helm_plan_dims.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(S), ctypes.POINTER(S)]
+    lib.helm_workspace_size.argtypes = [P, I, I, I, I, ctypes.POINTER(S)]
+    lib.helm_apply.argtypes = [P, P, D, I, I, P, P, I, P, S, P]
+    lib.helm_forward.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, S,
+                                 ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_adjoint.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, S,
+                                 ctypes.POINTER(HelmRhsReport), P]
+    lib.misfit_and_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, S,
+                                        ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_status_string.argtypes = [I]
+    lib.helm_status_string.restype = ctypes.c_char_p
+    lib.helm_kernel_launch_count.argtypes = []
+    lib.helm_kernel_launch_count.restype = ctypes.c_uint64
+    lib.helm_profile_enable.argtypes = [I]
+    lib.helm_profile_read.argtypes = [I, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(D),
+                                      ctypes.POINTER(D)]
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class HelmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {lib().helm_status_string(code).decode()} ({code})")
+
+
+def _check(code: int, where: str, allow_noconv: bool = False):
+    if code == HELM_OK or (allow_noconv and code == HELM_E_NOCONV):
+        return code
+    raise HelmError(code, where)
+
+
+def default_opts(**kw) -> HelmSolveOpts:
+    o = HelmSolveOpts()
+    lib().helm_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def make_grid(dim: int, n: Sequence[int], h: float, npml: Sequence[int], v_ref: float,
+              levels: int = 1, sigma_max: Sequence[float] = (0.0, 0.0, 0.0)) -> HelmGrid:
+    g = HelmGrid()
+    g.dim = dim
+    g.n[:] = list(n)
+    g.h = h
+    g.npml[:] = list(npml)
+    g.v_ref = v_ref
+    g.sigma_max[:] = list(sigma_max)
+    g.levels = levels
+    return g
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Plan:
+    """A helm_plan plus a cached caller-owned workspace."""
+
+    def __init__(self, grid: HelmGrid, opts: Optional[HelmSolveOpts] = None, device="cuda"):
+        self.grid = grid
+        self.opts = opts if opts is not None else default_opts()
+        self.device = torch.device(device)
+        h = ctypes.c_void_p()
+        _check(lib().helm_plan_create(ctypes.byref(grid), ctypes.byref(self.opts), ctypes.byref(h)),
+               "helm_plan_create")
+        self._h = h
+        N = (ctypes.c_int * 3)()
+        nc, nph = ctypes.c_size_t(), ctypes.c_size_t()
+        lib().helm_plan_dims(h, N, ctypes.byref(nc), ctypes.byref(nph))
+        self.N = tuple(N)
+        self.n_comp = nc.value
+        self.n_phys = nph.value
+        self._ws: Optional[torch.Tensor] = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().helm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def comp_shape(self):
+        return (self.N[2], self.N[1], self.N[0])
+
+    def workspace_size(self, call: int, nfreq: int, nsrc: int, nrec: int) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().helm_workspace_size(self._h, call, nfreq, nsrc, nrec, ctypes.byref(b)),
+               "helm_workspace_size")
+        return b.value
+
+    def workspace(self, nbytes: int):
+        """Device scratch of at least nbytes, 256-byte aligned (grown on demand)."""
+        if self._ws is None or self._ws.numel() < nbytes + 256:
+            self._ws = None
+            self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        p = self._ws.data_ptr()
+        off = (-p) % 256
+        return ctypes.c_void_p(p + off), self._ws.numel() - off
+
+
+def _need(cond: bool, msg: str):
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_common(plan: "Plan", m_phys, src_idx=None, Q=None, wavelet=None, nfreq=None):
+    _need(m_phys.numel() == plan.n_phys, f"m_phys must hold n_phys={plan.n_phys} values")
+    if Q is not None:
+        _need(Q.dim() == 2 and Q.shape[0] == src_idx.numel(), "Q must be [n_srcloc, nsrc]")
+    if wavelet is not None:
+        _need(wavelet.numel() == nfreq, "wavelet must hold one value per frequency")
+
+
+def _freqs(freqs_hz) -> ctypes.Array:
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64).ravel())
+    return (ctypes.c_double * len(f))(*f.tolist())
+
+
+def helm_apply(plan: Plan, m_phys: torch.Tensor, freq_hz: float, x: torch.Tensor, adjoint: bool = False,
+               out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """y = H x (or H^H x) for x of shape (nrhs, n_comp) complex128 (FP64) or complex64."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _check_common(plan, m_phys)
+    if x.dtype == torch.complex128:
+        prec = FP64
+    elif x.dtype == torch.complex64:
+        prec = MIXED
+    else:
+        raise TypeError("x must be complex128 or complex64")
+    _dev(x, x.dtype, "x")
+    nrhs = x.numel() // plan.n_comp
+    if nrhs * plan.n_comp != x.numel():
+        raise ValueError("x must hold whole fields")
+    y = torch.empty_like(x) if out is None else out
+    _need(y.dtype == x.dtype and y.numel() == x.numel() and y.is_contiguous() and y.data_ptr() != x.data_ptr(),
+          "out must be a distinct contiguous tensor like x")
+    ws, nb = plan.workspace(plan.workspace_size(CALL_APPLY, 1, nrhs, 0))
+    _check(lib().helm_apply(plan._h, _ptr(m_phys), float(freq_hz), int(bool(adjoint)), prec, _ptr(x),
+                            _ptr(y), nrhs, ws, nb, _stream(x.device)), "helm_apply")
+    return y
+
+
+def _reports(n):
+    return (HelmRhsReport * n)()
+
+
+def reports_to_list(rep):
+    return [dict(status=r.status, iters=r.iters, refinements=r.refinements, rel_resid=r.rel_resid)
+            for r in rep]
+
+
+def helm_forward(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, wavelet=None, want_fields=True,
+                 want_data=True):
+    """Returns (U [nfreq, nsrc, n_comp] or None, D [nfreq, nsrc, nrec] or None, reports)."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(src_idx, torch.int32, "src_idx")
+    _dev(Q, torch.complex128, "Q")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    if wavelet is not None:
+        _dev(wavelet, torch.complex128, "wavelet")
+    nfreq = len(np.atleast_1d(freqs_hz))
+    _check_common(plan, m_phys, src_idx, Q, wavelet, nfreq)
+    nsrc = Q.shape[1]
+    nrec = rec_idx.numel()
+    dev = m_phys.device
+    U = torch.empty((nfreq, nsrc, plan.n_comp), dtype=torch.complex128, device=dev) if want_fields else None
+    D = torch.empty((nfreq, nsrc, nrec), dtype=torch.complex128, device=dev) if want_data else None
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_FORWARD, nfreq, nsrc, nrec))
+    code = lib().helm_forward(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx), src_idx.numel(),
+                              _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(U), _ptr(D), ws, nb, rep,
+                              _stream(dev))
+    _check(code, "helm_forward", allow_noconv=True)
+    return U, D, reports_to_list(rep)
+
+
+def helm_adjoint(plan: Plan, m_phys, freqs_hz, rec_idx, R_in):
+    """V = H^{-H} P_r^T R for R_in [nfreq, nsrc, nrec]; returns (V, reports)."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    _dev(R_in, torch.complex128, "R_in")
+    _check_common(plan, m_phys)
+    _need(R_in.dim() == 3 and R_in.shape[0] == len(np.atleast_1d(freqs_hz)) and R_in.shape[2] == rec_idx.numel(),
+          "R_in must be [nfreq, nsrc, nrec]")
+    nfreq, nsrc, nrec = R_in.shape
+    V = torch.empty((nfreq, nsrc, plan.n_comp), dtype=torch.complex128, device=m_phys.device)
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_ADJOINT, nfreq, nsrc, nrec))
+    code = lib().helm_adjoint(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(rec_idx), nrec, _ptr(R_in),
+                              nsrc, _ptr(V), ws, nb, rep, _stream(m_phys.device))
+    _check(code, "helm_adjoint", allow_noconv=True)
+    return V, reports_to_list(rep)
+
+
+def misfit_and_gradient(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, mask=None,
+                        f_out=None, g_out=None):
+    """Returns (f [1] float64, g [n_phys] float64, reports); all device tensors."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(src_idx, torch.int32, "src_idx")
+    _dev(Q, torch.complex128, "Q")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    _dev(d_obs, torch.complex128, "d_obs")
+    if wavelet is not None:
+        _dev(wavelet, torch.complex128, "wavelet")
+    if mask is not None:
+        _dev(mask, torch.uint8, "mask")
+    nfreq = len(np.atleast_1d(freqs_hz))
+    _check_common(plan, m_phys, src_idx, Q, wavelet, nfreq)
+    nsrc = Q.shape[1]
+    nrec = rec_idx.numel()
+    _need(tuple(d_obs.shape) == (nfreq, nsrc, nrec), "d_obs must be [nfreq, nsrc, nrec]")
+    if mask is not None:
+        _need(mask.numel() == nfreq * nsrc, "mask must be [nfreq, nsrc]")
+    dev = m_phys.device
+    f = torch.empty(1, dtype=torch.float64, device=dev) if f_out is None else f_out
+    g = torch.empty(plan.n_phys, dtype=torch.float64, device=dev) if g_out is None else g_out
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_MISFIT_GRAD, nfreq, nsrc, nrec))
+    code = lib().misfit_and_gradient(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx),
+                                     src_idx.numel(), _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec,
+                                     _ptr(d_obs), _ptr(mask), _ptr(f), _ptr(g), ws, nb, rep, _stream(dev))
+    _check(code, "misfit_and_gradient", allow_noconv=True)
+    return f, g, reports_to_list(rep)
+
+
+def kernel_launch_count() -> int:
+    return int(lib().helm_kernel_launch_count())
+
+
+def profile_enable(on: bool = True):
+    lib().helm_profile_enable(int(bool(on)))
+
+
+def profile_read() -> dict:
+    out = {}
+    for i, name in enumerate(PROF_CLASSES):
+        n, ms, by = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+        lib().helm_profile_read(i, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by))
+        out[name] = dict(launches=int(n.value), ms=float(ms.value), bytes=float(by.value))
+    return out

@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI: the library loads, exports every function
+include/helm.h declares, and validates plans and sizes (no GPU calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import helmholtz as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_1703_09268_gb300", "libhelm.so")
+
+
+@pytest.fixture(scope="module")
+def helm():
+    if not os.path.exists(LIB):
+        from paper_1703_09268_gb300 import build
+        build.build()
+    from paper_1703_09268_gb300 import helm as H
+    return H
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "helm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", src, flags=re.M))
+                  - {"if", "defined"})
+
+
+def test_every_declared_symbol_is_exported(helm):
+    names = declared_functions()
+    assert "misfit_and_gradient" in names and "helm_forward" in names and "helm_adjoint" in names
+    lib = ctypes.CDLL(LIB)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(helm.EXPORTS) <= set(names)
+
+
+def test_plan_dims_match_grid_rule(helm):
+    for dim, n, npml, levels in [(3, (64, 64, 64), (10, 10, 10), 2), (3, (48, 50, 52), (10, 7, 12), 3),
+                                 (2, (101, 1, 101), (20, 0, 20), 2), (3, (20, 21, 22), (3, 4, 5), 1)]:
+        o = helm.default_opts(precond=helm.PRECOND_MLGMRES if levels > 1 else helm.PRECOND_NONE)
+        p = helm.Plan(helm.make_grid(dim, n, 25.0, npml, 3000.0, levels=levels), o, device="cpu")
+        g = O.make_grid(dim, n, 25.0, npml, 3000.0, levels=levels)
+        assert p.N == g.N
+        assert p.n_comp == g.size and p.n_phys == g.n_phys
+        if levels > 1:
+            for d in range(3):
+                if g.N[d] > 1:
+                    assert (p.N[d] + 1) % (1 << (levels - 1)) == 0
+        p.close()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(h=0.0), dict(h=-1.0), dict(levels=0), dict(levels=4), dict(npml=(-1, 2, 2)),
+    dict(n=(1, 8, 8)), dict(v_ref=0.0),
+])
+def test_invalid_grid_rejected(helm, bad):
+    args = dict(dim=3, n=(8, 8, 8), h=10.0, npml=(2, 2, 2), v_ref=2000.0, levels=1)
+    args.update(bad)
+    g = helm.make_grid(args["dim"], args["n"], args["h"], args["npml"], args["v_ref"], levels=args["levels"])
+    o = helm.default_opts(precond=helm.PRECOND_NONE)
+    h = ctypes.c_void_p()
+    code = helm.lib().helm_plan_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h))
+    assert code == helm.HELM_E_INVAL and not h.value
+
+
+@pytest.mark.parametrize("bad", [
+    dict(precision=7), dict(precond=9), dict(k_inner=0), dict(k_inner=33), dict(tol=0.0), dict(tol=1.5),
+    dict(max_cycles=0), dict(tol_inner=0.0), dict(max_refine=0), dict(k_si=0), dict(k_ci=40),
+    dict(max_batch=-1),
+])
+def test_invalid_options_rejected(helm, bad):
+    g = helm.make_grid(3, (8, 8, 8), 10.0, (2, 2, 2), 2000.0, levels=2)
+    o = helm.default_opts(**bad)
+    h = ctypes.c_void_p()
+    assert helm.lib().helm_plan_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == helm.HELM_E_INVAL
+
+
+def test_mlgmres_needs_levels_and_coarse_size(helm):
+    o = helm.default_opts(precond=helm.PRECOND_MLGMRES)
+    h = ctypes.c_void_p()
+    g1 = helm.make_grid(3, (8, 8, 8), 10.0, (2, 2, 2), 2000.0, levels=1)
+    assert helm.lib().helm_plan_create(ctypes.byref(g1), ctypes.byref(o), ctypes.byref(h)) == helm.HELM_E_INVAL
+    g3 = helm.make_grid(3, (2, 2, 2), 10.0, (0, 0, 0), 2000.0, levels=3)
+    assert helm.lib().helm_plan_create(ctypes.byref(g3), ctypes.byref(o), ctypes.byref(h)) == helm.HELM_E_INVAL
+
+
+def test_workspace_sizes(helm):
+    p = helm.Plan(helm.make_grid(3, (16, 16, 16), 25.0, (4, 4, 4), 3000.0, levels=2), helm.default_opts(),
+                  device="cpu")
+    a = p.workspace_size(helm.CALL_APPLY, 1, 4, 0)
+    f1 = p.workspace_size(helm.CALL_FORWARD, 1, 4, 16)
+    f2 = p.workspace_size(helm.CALL_FORWARD, 1, 8, 16)
+    m = p.workspace_size(helm.CALL_MISFIT_GRAD, 1, 8, 16)
+    assert 0 < a < f1 < f2 < m
+    # batching bounds the workspace
+    pb = helm.Plan(helm.make_grid(3, (16, 16, 16), 25.0, (4, 4, 4), 3000.0, levels=2),
+                   helm.default_opts(max_batch=2), device="cpu")
+    assert pb.workspace_size(helm.CALL_FORWARD, 1, 8, 16) < f2
+    with pytest.raises(helm.HelmError):
+        p.workspace_size(helm.CALL_FORWARD, 0, 4, 16)
+
+
+def test_status_strings(helm):
+    L = helm.lib()
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert L.helm_status_string(code)
+    assert L.helm_status_string(123) == b"unknown status"
