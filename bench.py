@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark: frequency-domain FWI misfit + adjoint-state gradient throughput.
+
+One step = f and g = E^T sum_s w^2 Re(conj(u_s) v_s) over every (source,
+frequency) pair of the workload: 2 batched Helmholtz solves per pair (forward
+and adjoint), complex64 FGMRES + ML-GMRES inner solves inside FP64 iterative
+refinement, receiver restriction, adjoint sources and gradient accumulation,
+all in libhelm.so's kernels.
+
+Workload (N=1): 64^3 physical grid, h = 25 m, 10-cell damping layer, seeded
+layered velocity 1500-4500 m/s smoothed (sigma 2 cells), 4 Hz, 16 point
+sources on a 4x4 grid at z = 50 m, receivers at every surface node.  With N
+ranks (torchrun) every rank evaluates its own 16 sources and the ranks sum f
+and g with one all-reduce (the paper's sum over workers): weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "misfit+gradient (src·freq)/s and stencil Gpts/s, % HBM roofline, at ≤1e-8 rel err"
+UNIT = "(src·freq)/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precond", default="mlgmres", choices=["mlgmres", "jacobi", "none"])
+    p.add_argument("--levels", type=int, default=2)
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--n", type=int, default=64)
+    p.add_argument("--no-fp64-baseline", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def workload(n, rank, world):
+    """16 sources per rank on a (4*world) x 4 surface grid; rank r takes every world-th."""
+    from paper_1703_09268_gb300 import synth
+    wl = synth.workload_3d_layered(n=n, h=25.0 * 64 / n)
+    if world > 1:
+        nx_s = 4 * world
+        nodes = [(int((i + 0.5) * n / nx_s), int((j + 0.5) * n / 4), 2) for j in range(4) for i in range(nx_s)]
+        nodes = nodes[rank::world]
+        wl.src_idx, wl.Q = synth.point_sources(wl.n, nodes)
+    return wl
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle's restarted GMRES on the same operator
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    n, seconds, seed = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    import numpy as _np
+    from oracle import helmholtz as O
+    from paper_1703_09268_gb300 import synth
+    wl = synth.workload_3d_layered(n=n, h=25.0 * 64 / n)
+    g = O.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=2)
+    t0 = time.time()
+    H = O.helmholtz_matrix(g, O.extend(g, wl.m0), 2 * _np.pi * wl.freqs_hz[0])
+    q = O.source_fields(g, wl.src_idx, wl.Q)[seed % wl.nsrc]
+    t_setup = time.time() - t0
+    # bounded sample: GMRES(60) cycles until the time budget is spent
+    it_total, t_run = 0, 0.0
+    x = None
+    while t_run < seconds:
+        t1 = time.time()
+        x, it, _ = O.gmres(H, q, tol=1e-30, restart=60, maxiter=60, x0=x)
+        t_run += time.time() - t1
+        it_total += it
+    return dict(iters=it_total, seconds=t_run, setup=t_setup)
+
+
+def cpu_baseline(n, seconds):
+    """(src.freq)/s of the oracle on the host cores: a bounded sample of GMRES
+    iterations on the full-size operator in one spawned process per core,
+    scaled by the oracle's own iteration count for a forward + adjoint solve."""
+    import multiprocessing as mp
+    path = os.path.join(ROOT, "oracle", "data", f"gmres_iterations_3d_layered_{n}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        iters = json.load(fh)
+    per_pair_iters = iters["forward_iterations"] + iters["adjoint_iterations"]
+    procs = max(1, min(os.cpu_count() or 1, 16))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(n, seconds, i) for i in range(procs)])
+    t_iter = float(np.mean([r["seconds"] / r["iters"] for r in res]))
+    pair_seconds = per_pair_iters * t_iter
+    value = procs / pair_seconds
+    return dict(value=value, unit=UNIT, cores=procs, kind="oracle",
+                sample=(f"{procs} spawned single-thread processes, each running the oracle's GMRES(60) on the "
+                        f"full {iters['grid']} operator for ~{seconds:.0f} s ({int(np.mean([r['iters'] for r in res]))} "
+                        f"iterations, {t_iter*1e3:.1f} ms each); scaled by the oracle's {per_pair_iters} iterations "
+                        f"for one forward + adjoint solve to tol {iters['tol']:g} "
+                        f"(oracle/data/{os.path.basename(path)}); assembly excluded"))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.n, max(2.0, args.cpu_seconds / 3))
+        if i >= args.warmup:
+            steps.append(cb["value"])
+    v = float(np.median(steps))
+    cb["value"] = v
+    line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * 16 / v, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=f"3d-layered-{args.n}^3-h25-pml10-4Hz-16src", sources=16, freqs=1),
+                cpu_baseline=cb, e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unavailable"])
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the oracle's process pool is spawned before the first GPU call
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.n, args.cpu_seconds)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1703_09268_gb300 import helm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    wl = workload(args.n, rank, world)
+    levels = args.levels if args.precond == "mlgmres" else max(1, args.levels)
+    grid = helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=levels)
+    prec = {"mlgmres": helm.PRECOND_MLGMRES, "jacobi": helm.PRECOND_JACOBI, "none": helm.PRECOND_NONE}[args.precond]
+    kin = 5 if prec == helm.PRECOND_MLGMRES else 30
+    opts = helm.default_opts(precision=helm.MIXED if args.precision == "mixed" else helm.FP64, precond=prec,
+                             k_inner=kin, tol=args.tol, max_cycles=400)
+    plan = helm.Plan(grid, opts, device=dev)
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    m0 = T(wl.m0.ravel(), torch.float64)
+    src = T(wl.src_idx, torch.int32)
+    Q = T(wl.Q, torch.complex128)
+    rec = T(wl.rec_idx, torch.int32)
+    # observed data: FP64 forward modelling in the true model (input generation, untimed)
+    p64 = helm.Plan(grid, helm.default_opts(precision=helm.FP64, precond=helm.PRECOND_MLGMRES, tol=1e-13,
+                                            max_cycles=400), device=dev)
+    _, d_obs, _ = helm.helm_forward(p64, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
+                                    want_fields=False)
+    nsrc, nfreq = wl.nsrc, wl.nfreq
+    units = nsrc * nfreq
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(p=plan, reduce=True):
+        f, g, rep = helm.misfit_and_gradient(p, m0, wl.freqs_hz, src, Q, rec, d_obs)
+        if world > 1 and reduce:
+            dist.all_reduce(f)
+            dist.all_reduce(g)
+        return f, g, rep
+
+    for _ in range(args.warmup):
+        f, g, rep = step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = helm.kernel_launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (256 MB > 129 MB L2), outside the events
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, g, rep = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    launches = helm.kernel_launch_count() - launches0
+    ms = float(np.mean(times))
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = units * world / (ms_max / 1e3)
+    iters = [r["iters"] for r in rep]
+    refs = [r["refinements"] for r in rep]
+
+    # one profiled step: per-kernel-class device time and algorithmic bytes
+    helm.profile_enable(True)
+    flush.zero_()
+    torch.cuda.synchronize()
+    step(reduce=False)
+    torch.cuda.synchronize()
+    prof = helm.profile_read()
+    helm.profile_enable(False)
+    hbm, hbm_kind = peaks()
+    tot_ms = sum(v["ms"] for v in prof.values())
+    dom = max((k for k in prof if prof[k]["bytes"] > 0), key=lambda k: prof[k]["ms"])
+    dn = prof[dom]
+    achieved = dn["bytes"] / (dn["ms"] / 1e3) / 1e9
+    roofline = dict(bound="hbm", kernel=dom, achieved=round(achieved, 1), peak=hbm, unit="GB/s",
+                    frac=round(achieved / hbm, 3), traffic=None, peak_kind=hbm_kind,
+                    launches=dn["launches"], avg_launch_us=round(1e3 * dn["ms"] / max(dn["launches"], 1), 2),
+                    bytes_per_launch=dn["bytes"] / max(dn["launches"], 1),
+                    share={k: round(v["ms"] / tot_ms, 3) for k, v in prof.items() if v["launches"]})
+    st = prof["stencil_c64"] if prof["stencil_c64"]["launches"] else prof["stencil_c128"]
+    sbytes_pt = 16.0 if prof["stencil_c64"]["launches"] else 32.0
+    stencil = dict(gpts=round(st["bytes"] / sbytes_pt / (st["ms"] / 1e3) / 1e9, 1),
+                   gbs=round(st["bytes"] / (st["ms"] / 1e3) / 1e9, 1),
+                   frac=round(st["bytes"] / (st["ms"] / 1e3) / 1e9 / hbm, 3),
+                   launches=st["launches"], avg_launch_us=round(1e3 * st["ms"] / max(st["launches"], 1), 2))
+
+    out = dict(metric=METRIC, value=round(value, 3), unit=UNIT, n_gpus=world, steps=args.steps,
+               warmup=args.warmup, ms_per_step=round(ms_max, 3), higher_is_better=True, scaling="weak",
+               vs_baseline=None, dtype="c64 inner / f64 refine" if args.precision == "mixed" else "f64",
+               data="synthetic (seeded layered model, observed data modelled in FP64)",
+               config=dict(workload=wl.name if world == 1 else f"{wl.name}-x{world}ranks", grid_comp=list(plan.N),
+                           sources_per_rank=nsrc, freqs=nfreq, receivers=wl.nrec, precond=args.precond,
+                           levels=levels, k_inner=kin, tol=args.tol, l2="flushed between timed steps (256 MB)",
+                           parallelism=f"dp{world} over sources, f and g all-reduced" if world > 1 else "1 GPU"),
+               roofline=roofline, stencil=stencil, gpu_launches=int(launches),
+               solver=dict(outer_iters_per_pair=float(np.mean(iters)), refinements_per_pair=float(np.mean(refs)),
+                           max_rel_resid=float(max(r["rel_resid"] for r in rep))),
+               clocks=clk)
+    if rank == 0:
+        # accuracy against the FP64 GPU path (itself checked against the oracle in tests)
+        if args.precision == "mixed":
+            f64, g64, _ = helm.misfit_and_gradient(p64, m0, wl.freqs_hz, src, Q, rec, d_obs)
+            f1, g1, _ = step(reduce=False)
+            out["accuracy"] = dict(
+                reference="FP64 GPU path, FGMRES+ML-GMRES to rel. residual 1e-13",
+                f_rel_err=float(abs(f1.item() - f64.item()) / abs(f64.item())),
+                g_rel_err=float((g1 - g64).norm().item() / g64.norm().item()))
+        if not args.no_fp64_baseline:
+            pb = helm.Plan(grid, helm.default_opts(precision=helm.FP64, precond=prec, k_inner=kin, tol=args.tol,
+                                                   max_cycles=400, max_batch=1), device=dev)
+            helm.misfit_and_gradient(pb, m0, wl.freqs_hz, src, Q, rec, d_obs)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            helm.misfit_and_gradient(pb, m0, wl.freqs_hz, src, Q, rec, d_obs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t64 = e0.elapsed_time(e1)
+            out["fp64_per_source"] = dict(value=round(units / (t64 / 1e3), 3), unit=UNIT, ms_per_step=round(t64, 1),
+                                          speedup_of_value=round(value / (units / (t64 / 1e3)), 2),
+                                          what="FP64 FGMRES+same preconditioner, one right-hand side at a time")
+        # end to end through the public API with host buffers
+        hm = torch.as_tensor(wl.m0.ravel(), dtype=torch.float64).pin_memory()
+        hd = d_obs.cpu().pin_memory()
+        hs, hq, hr = src.cpu().pin_memory(), Q.cpu().pin_memory(), rec.cpu().pin_memory()
+        e2e_t = []
+        for i in range(args.steps + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dm, dd = hm.to(dev, non_blocking=True), hd.to(dev, non_blocking=True)
+            ds, dq, dr = hs.to(dev, non_blocking=True), hq.to(dev, non_blocking=True), hr.to(dev, non_blocking=True)
+            f, g, _ = helm.misfit_and_gradient(plan, dm, wl.freqs_hz, ds, dq, dr, dd)
+            fh, gh = f.cpu(), g.cpu()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i > 0:
+                e2e_t.append(e0.elapsed_time(e1))
+        h2d = sum(t.numel() * t.element_size() for t in (hm, hd, hs, hq, hr))
+        d2h = fh.numel() * 8 + gh.numel() * 8
+        out["e2e"] = dict(value=round(units / (np.mean(e2e_t) / 1e3), 3), unit=UNIT, h2d_bytes_per_step=int(h2d),
+                          d2h_bytes_per_step=int(d2h))
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -105,9 +105,9 @@ def wl2d():
 
 
 OPTS = {
-    "fp64-mlgmres": dict(precision=0, precond=2, tol=1e-13),
-    "fp64-none": dict(precision=0, precond=0, k_inner=30, tol=1e-13, max_cycles=2000),
-    "fp64-jacobi": dict(precision=0, precond=1, k_inner=20, tol=1e-13, max_cycles=2000, jacobi_sweeps=2),
+    "fp64-mlgmres": dict(precision=0, precond=2, tol=1e-14),
+    "fp64-none": dict(precision=0, precond=0, k_inner=30, tol=1e-14, max_cycles=2000),
+    "fp64-jacobi": dict(precision=0, precond=1, k_inner=20, tol=1e-14, max_cycles=2000, jacobi_sweeps=2),
     "mixed-mlgmres": dict(precision=1, precond=2, tol=1e-11),
     "mixed-none": dict(precision=1, precond=0, k_inner=30, tol=1e-11, max_cycles=400),
 }

@@ -1,0 +1,98 @@
+"""World-size-2 gloo ranks on the CPU: the source partition plus one sum
+reproduces the single-rank misfit and gradient, and a rank that never reports
+is dropped from the sum after the deadline (Sec. 3 worker-timeout proposal).
+The per-rank work is the CPU oracle on a small 2D problem; no GPU is used."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from oracle import helmholtz as O
+from paper_1703_09268_gb300 import parallel
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _problem():
+    rng = np.random.default_rng(4)
+    n = 25
+    g = O.make_grid(2, (n, 1, n), 25.0, (6, 0, 6), 2500.0)
+    v = 2000 + 300 * rng.random((n, 1, n))
+    mt = 1 / v ** 2
+    m0 = np.full(g.phys_shape, 1 / 2150 ** 2)
+    src = np.array([2 + n * 2, 8 + n * 2, 12 + n * 2, 18 + n * 2, 22 + n * 2], dtype=np.int32)
+    Q = np.eye(5, dtype=complex)
+    rec = (np.arange(n) + n * 1).astype(np.int32)
+    freqs = np.array([4.0, 7.0])
+    _, d = O.forward(g, mt, freqs, src, Q, rec)
+    return g, m0, freqs, src, Q, rec, d
+
+
+def _rank_work(rank, world, mask_pairs):
+    g, m0, freqs, src, Q, rec, d = _problem()
+    nf, ns = len(freqs), Q.shape[1]
+    mine = parallel.shard(nf * ns, rank, world)
+    mask = np.zeros((nf, ns), dtype=bool)
+    for p in mine:
+        if mask_pairs is None or p in mask_pairs:
+            mask[p // ns, p % ns] = True
+    f, gr = O.misfit_and_gradient(g, m0, freqs, src, Q, rec, d, mask=mask)
+    return f, gr
+
+
+def _worker_allreduce(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    f, gr = _rank_work(rank, world, None)
+    tf = torch.tensor([f], dtype=torch.float64)
+    tg = torch.from_numpy(gr.ravel().copy())
+    parallel.allreduce_sum([tf, tg])
+    if rank == 0:
+        np.save(out, np.concatenate([tf.numpy(), tg.numpy()]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _worker_deadline(rank, world, port, out):
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=__import__("datetime").timedelta(seconds=30))
+    f, gr = _rank_work(rank, world, None)
+    if rank == 1:
+        return  # this worker "fails": it never publishes its contribution
+    sums, got = parallel.sum_with_deadline(store, "step0", rank, world, [np.array([f]), gr.ravel()], 2.0)
+    np.save(out, np.concatenate([sums[0], sums[1], np.array(got, dtype=float)]))
+
+
+def test_shard_covers_every_pair_once():
+    for units in (1, 5, 16, 17):
+        for world in (1, 2, 3, 8):
+            seen = sorted(sum((parallel.shard(units, r, world) for r in range(world)), []))
+            assert seen == list(range(units))
+
+
+def test_two_rank_allreduce_equals_single_rank(tmp_path):
+    out = str(tmp_path / "ar.npy")
+    mp.spawn(_worker_allreduce, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    g, m0, freqs, src, Q, rec, d = _problem()
+    f, gr = O.misfit_and_gradient(g, m0, freqs, src, Q, rec, d)
+    assert got[0] == pytest.approx(f, rel=1e-13)
+    assert np.allclose(got[1:], gr.ravel(), rtol=1e-12, atol=1e-12 * np.abs(gr).max())
+
+
+def test_late_rank_is_dropped_after_deadline(tmp_path):
+    out = str(tmp_path / "dl.npy")
+    mp.spawn(_worker_deadline, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    f0, g0 = _rank_work(0, 2, None)
+    n = g0.size
+    assert got[0] == pytest.approx(f0, rel=1e-13)
+    assert np.allclose(got[1:1 + n], g0.ravel())
+    assert list(got[1 + n:]) == [0.0]
