@@ -49,7 +49,39 @@ def parse():
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--mode", default="step", choices=["step", "apply"],
+                   help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
+                        "workload's 16 complex64 fields)")
     return p.parse_args()
+
+
+def run_apply(args):
+    """Stencil microbenchmark: y = H x for the workload's 16 fields, complex64 and complex128."""
+    import torch
+    from paper_1703_09268_gb300 import helm
+    dev = torch.device("cuda", 0)
+    wl = workload(args.n, 0, 1)
+    plan = helm.Plan(helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=args.levels), helm.default_opts(),
+                     device=dev)
+    m0 = torch.as_tensor(wl.m0.ravel(), dtype=torch.float64, device=dev)
+    hbm, kind = peaks()
+    out = dict(mode="apply", workload=wl.name, grid_comp=list(plan.N), fields=wl.nsrc)
+    for name, dt, bpp in (("c64", torch.complex64, 16.0), ("c128", torch.complex128, 32.0)):
+        x = torch.randn(wl.nsrc, plan.n_comp, dtype=dt, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(args.warmup):
+            helm.helm_apply(plan, m0, wl.freqs_hz[0], x, out=y)
+        helm.profile_enable(True)
+        for _ in range(args.steps):
+            helm.helm_apply(plan, m0, wl.freqs_hz[0], x, out=y)
+        prof = helm.profile_read()
+        helm.profile_enable(False)
+        st = prof["stencil_" + name]
+        t = st["ms"] / 1e3
+        out[name] = dict(gpts=round(st["bytes"] / bpp / t / 1e9, 1), gbs=round(st["bytes"] / t / 1e9, 1),
+                         frac=round(st["bytes"] / t / 1e9 / hbm, 3), us_per_launch=round(1e6 * t / st["launches"], 2),
+                         peak=hbm, peak_kind=kind)
+    print(json.dumps(out), flush=True)
 
 
 def peaks():
@@ -194,6 +226,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "apply":
+        return run_apply(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
