@@ -45,6 +45,11 @@ def parse():
     p.add_argument("--precond", default="mlgmres", choices=["mlgmres", "jacobi", "none"])
     p.add_argument("--levels", type=int, default=2)
     p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--tol-inner", type=float, default=1e-4)
+    p.add_argument("--k-inner", type=int, default=0, help="outer FGMRES cycle length (0: 5 with ML-GMRES, else 30)")
+    p.add_argument("--reorth", type=int, default=1)
+    p.add_argument("--max-batch", type=int, default=0, help="right-hand sides solved together (0 = all)")
+    p.add_argument("--smoother", default="3,5,3,5", help="ML-GMRES (k_so, k_si, k_co, k_ci)")
     p.add_argument("--n", type=int, default=64)
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -248,9 +253,11 @@ def main():
     levels = args.levels if args.precond == "mlgmres" else max(1, args.levels)
     grid = helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=levels)
     prec = {"mlgmres": helm.PRECOND_MLGMRES, "jacobi": helm.PRECOND_JACOBI, "none": helm.PRECOND_NONE}[args.precond]
-    kin = 5 if prec == helm.PRECOND_MLGMRES else 30
+    kin = args.k_inner or (5 if prec == helm.PRECOND_MLGMRES else 30)
+    kso, ksi, kco, kci = (int(v) for v in args.smoother.split(","))
     opts = helm.default_opts(precision=helm.MIXED if args.precision == "mixed" else helm.FP64, precond=prec,
-                             k_inner=kin, tol=args.tol, max_cycles=400)
+                             k_inner=kin, tol=args.tol, max_cycles=400, tol_inner=args.tol_inner, max_refine=60,
+                             reorth=args.reorth, k_so=kso, k_si=ksi, k_co=kco, k_ci=kci, max_batch=args.max_batch)
     plan = helm.Plan(grid, opts, device=dev)
     T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
     m0 = T(wl.m0.ravel(), torch.float64)
@@ -334,7 +341,8 @@ def main():
                data="synthetic (seeded layered model, observed data modelled in FP64)",
                config=dict(workload=wl.name if world == 1 else f"{wl.name}-x{world}ranks", grid_comp=list(plan.N),
                            sources_per_rank=nsrc, freqs=nfreq, receivers=wl.nrec, precond=args.precond,
-                           levels=levels, k_inner=kin, tol=args.tol, l2="flushed between timed steps (256 MB)",
+                           levels=levels, k_inner=kin, smoother=args.smoother, tol=args.tol,
+                           tol_inner=args.tol_inner, reorth=args.reorth, l2="flushed between timed steps (256 MB)",
                            parallelism=f"dp{world} over sources, f and g all-reduced" if world > 1 else "1 GPU"),
                roofline=roofline, stencil=stencil, gpu_launches=int(launches),
                solver=dict(outer_iters_per_pair=float(np.mean(iters)), refinements_per_pair=float(np.mean(refs)),

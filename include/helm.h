@@ -98,6 +98,13 @@ typedef struct {
   double jacobi_omega;   /* damped-Jacobi weight */
   int jacobi_sweeps;     /* damped-Jacobi sweeps per preconditioner application */
   int max_batch;         /* right-hand sides solved together (0 = all at once) */
+  int reorth;            /* 1: Gram-Schmidt with one re-orthogonalisation pass (CGS2);
+                            0: a single classical Gram-Schmidt pass */
+  int sstep;             /* 1: the fixed-cycle GMRES solves (ML-GMRES smoothers and the
+                            last-level coarse solve) build their Krylov basis with s = k
+                            operator applications and solve the same minimal-residual
+                            problem through its Gram matrix (s-step GMRES; k <= 8);
+                            0: Arnoldi with Gram-Schmidt for every solve */
 } helm_solve_opts;
 
 /* One report per right-hand side (frequency-major, like the fields). */
@@ -111,7 +118,7 @@ typedef struct {
 typedef struct helm_plan helm_plan;
 
 /* Fill `opts` with the defaults: MIXED, ML-GMRES (3,5,3,5), FGMRES(5),
- * tol 1e-10, tol_inner 1e-4.  Returns HELM_OK. */
+ * tol 1e-10, tol_inner 1e-4, CGS2.  Returns HELM_OK. */
 int helm_default_opts(helm_solve_opts* opts);
 
 /* Validate `grid` and `opts` and build a host-side plan (no device memory).

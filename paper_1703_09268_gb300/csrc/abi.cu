@@ -107,6 +107,8 @@ static int build_plan(const helm_grid* g, const helm_solve_opts* o, helm_plan* P
   if (o->precond == HELM_PRECOND_JACOBI && (!(o->jacobi_omega > 0.0) || o->jacobi_sweeps < 1))
     return HELM_E_INVAL;
   if (o->max_batch < 0) return HELM_E_INVAL;
+  if (o->reorth != 0 && o->reorth != 1) return HELM_E_INVAL;
+  if (o->sstep != 0 && o->sstep != 1) return HELM_E_INVAL;
 
   std::memset(P, 0, sizeof(*P));
   P->g = *g;
@@ -209,6 +211,8 @@ int helm_default_opts(helm_solve_opts* o) {
   o->jacobi_omega = 0.6;
   o->jacobi_sweeps = 1;
   o->max_batch = 0;
+  o->reorth = 1;
+  o->sstep = 1;
   return HELM_OK;
 }
 

@@ -139,11 +139,16 @@ struct KState {
 // Kernel launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 
-// y = bs*b - xs*H x   (b == nullptr: y = xs*H x), for the active slots.
+struct Epi;  // fused reduction + per-slot epilogue (reduce.cuh)
+
+// y = bs*b - xs*H x   (b == nullptr: y = xs*H x), for the active slots.  With an
+// epilogue the kernel also reduces y: the norm (EPI_NORM / EPI_START) or the
+// dots with basis vectors V_0..V_{nv-1} (EPI_DOTS).
 template <typename R>
 void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int na,
                     const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y,
-                    cudaStream_t st);
+                    cudaStream_t st, const Epi* epi = nullptr, const cplx<R>* V = nullptr,
+                    size_t vstride = 0, int nv = 0);
 
 // Damped Jacobi: z = z + omega D^{-1}(bs*b - H z) (first sweep with z = 0 gives omega D^{-1} bs*b).
 template <typename R>
@@ -153,25 +158,18 @@ template <typename R>
 void launch_jacobi_update(const OpView<R>& op, const int* slot_f, const int* act, int na,
                           const cplx<R>* r, R omega, cplx<R>* z, cudaStream_t st);
 
-// Vector passes over basis vectors V_0..V_{nv-1} (V_i of slot s at V + i*vstride + s*n).
+// Vector passes over basis vectors V_0..V_{nv-1} (V_i of slot s at V + i*vstride + s*n),
+// each with its reduction folded into an epilogue.
 enum GsMode { GS_DOT = 0, GS_SUB_DOT = 1, GS_SUB_STORE_NORM = 2, GS_ADD_STORE = 3 };
-// Returns the number of blocks per slot used (partials layout [na][nblk][vals]).
 template <typename R>
-int launch_gs(int mode, const cplx<R>* V, size_t vstride, int nv, const cplx<R>* coef,
-              const cplx<R>* w, Scale<R> ws, cplx<R>* out, const int* act, int na, size_t n,
-              double* partial, cudaStream_t st);
-
-// Small per-slot kernels (double precision bookkeeping).
-void launch_red_dots(const double* partial, int nblk, int nv, const int* act, int na, KState ks,
-                     int accumulate, int rbytes, cudaStream_t st);
-void launch_red_norm_arnoldi(const double* partial, int nblk, const int* act, int na, KState ks,
-                             int j, int rbytes, cudaStream_t st);
-void launch_red_start(const double* partial, int nblk, const int* act, int na, KState ks,
-                      int set_bnorm, int rbytes, cudaStream_t st);
-void launch_red_norm(const double* partial, int nblk, const int* act, int na, double* out,
-                     cudaStream_t st);
-void launch_small_solve(const int* act, int na, KState ks, int k, int flexible, int rbytes,
-                        cudaStream_t st);
+void launch_gs(int mode, const cplx<R>* V, size_t vstride, int nv, const cplx<R>* coef,
+               const cplx<R>* w, Scale<R> ws, cplx<R>* out, const int* act, int na, size_t n,
+               const Epi& e, cudaStream_t st);
+int reduction_blocks(int na, size_t n, int threads);
+// Gram pass of an s-step cycle over W_0..W_s (EPI_GRAM epilogue).
+template <typename R>
+void launch_gram(const cplx<R>* V, size_t vstride, int s, const int* act, int na, size_t n, const Epi& e,
+                 cudaStream_t st);
 
 // Precision conversions and refinement helpers (slot-batched).
 void launch_to32_scaled(const double2* r, const double* rnorm, float2* out, const int* act, int na,

@@ -19,7 +19,14 @@
 #include <cmath>
 #include <cstring>
 
+#include "reduce.cuh"
 #include "solver.h"
+
+// 1: the first Gram-Schmidt pass of each Arnoldi step is folded into the
+// stencil launch; 0: it runs as its own streaming pass.
+#ifndef HELM_FUSE_DOTS
+#define HELM_FUSE_DOTS 1
+#endif
 
 namespace helm {
 
@@ -114,7 +121,10 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   C.ident = bp.take<int>(B);
   C.err = bp.take<int>(4);
   if (call == HELM_CALL_APPLY) return bp.off;
-  C.partial = bp.take<double>((size_t)std::max(RED_BLOCKS_MAX, B) * 2 * (KMAX + 1));
+  // partial rows: at most max(RED_BLOCKS_MAX, B) rows of at most max(2(KMAX+1), Gram) values
+  C.partial = bp.take<double>((size_t)std::max(RED_BLOCKS_MAX, B) *
+                              std::max(2 * (KMAX + 1), gram_nvals(SSTEP_MAX)));
+  C.counter = bp.take<unsigned>(B);
   const size_t n0 = P.lev[0].n;
   C.q = bp.take<double2>((size_t)B * n0);
   C.u = bp.take<double2>((size_t)B * n0);
@@ -195,6 +205,7 @@ int setup_operator(Ctx& c, const double* m_phys, const double* freqs_hz) {
   for (int i = 0; i < c.B; ++i) id[i] = i;
   cudaMemcpyAsync(c.ident, id.data(), sizeof(int) * c.B, cudaMemcpyHostToDevice, c.st);
   cudaMemsetAsync(c.err, 0, 4 * sizeof(int), c.st);
+  if (c.counter) cudaMemsetAsync(c.counter, 0, sizeof(unsigned) * c.B, c.st);
   launch_extend(P, m_phys, c.m64[0], c.m32[0], c.st);
   for (int l = 1; l < L; ++l) {
     launch_restrict_model(c.m64[l - 1], P.lev[l - 1], c.m64[l], P.lev[l], c.st);
@@ -225,15 +236,22 @@ template <typename R> static Hierarchy<R>& hier(Ctx& c);
 template <> Hierarchy<float>& hier<float>(Ctx& c) { return c.h32; }
 template <> Hierarchy<double>& hier<double>(Ctx& c) { return c.h64; }
 
-static inline int rbytes_of(float) { return 4; }
-static inline int rbytes_of(double) { return 8; }
+
+static Epi make_epi(Ctx& c, int kind, const KState* ks = nullptr) {
+  Epi e;
+  e.kind = kind;
+  if (ks) e.ks = *ks;
+  e.counter = c.counter;
+  e.partial = c.partial;
+  return e;
+}
 
 // ||bs*b|| of every active slot into out[slot]
 template <typename R>
 static void norms(Ctx& c, const cplx<R>* b, Scale<R> bs, size_t n, double* out) {
-  const int nb = launch_gs<R>(GS_SUB_STORE_NORM, nullptr, 0, 0, nullptr, b, bs, nullptr, c.act, c.na, n,
-                              c.partial, c.st);
-  launch_red_norm(c.partial, nb, c.act, c.na, out, c.st);
+  Epi e = make_epi(c, EPI_NORM);
+  e.out = out;
+  launch_gs<R>(GS_SUB_STORE_NORM, nullptr, 0, 0, nullptr, b, bs, nullptr, c.act, c.na, n, e, c.st);
 }
 
 using Prec32 = std::function<void(const cplx<float>*, Scale<float>, cplx<float>*)>;
@@ -255,27 +273,25 @@ template <typename R>
 static int krylov(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero,
                   int cycles, double tol, const typename PrecT<R>::T* prec, KrylovOut* out,
                   bool final_resid = false) {
-  const int rb = rbytes_of(R(0));
   const OpView<R> op = op_view<R>(c, I.level, c.dir);
   const size_t n = op.n;
   const size_t vs = (size_t)c.B * n;  // stride between basis vectors
   const int K1 = KMAX + 1;
   const std::vector<int> saved = c.act_h;
+  const bool reorth = c.P->o.reorth != 0;
   int status = HELM_OK;
   if (x0_zero) launch_zero<R>(x, c.act, c.na, n, c.st);
   if (tol > 0.0 && !x0_zero) norms<R>(c, b, bs, n, I.ks.bnorm);
   std::vector<double> rn(c.B), bn(c.B);
+  const bool flex = I.flex && prec;
   for (int cyc = 0; cyc < cycles && c.na > 0; ++cyc) {
-    // start vector V_0 = bs*b - H x (plain copy when x is still zero)
-    int nb;
-    if (cyc == 0 && x0_zero) {
-      nb = launch_gs<R>(GS_SUB_STORE_NORM, nullptr, 0, 0, nullptr, b, bs, I.V, c.act, c.na, n, c.partial, c.st);
-    } else {
-      launch_stencil<R>(op, c.slot_f, c.act, c.na, x, Scale<R>{}, b, bs, I.V, c.st);
-      nb = launch_gs<R>(GS_SUB_STORE_NORM, nullptr, 0, 0, nullptr, I.V, Scale<R>{}, nullptr, c.act, c.na, n,
-                        c.partial, c.st);
-    }
-    launch_red_start(c.partial, nb, c.act, c.na, I.ks, (tol > 0.0 && cyc == 0 && x0_zero) ? 1 : 0, rb, c.st);
+    // start vector V_0 = bs*b - H x (a plain copy while x is zero) and beta = ||V_0||
+    Epi es = make_epi(c, EPI_START, &I.ks);
+    es.set_bnorm = (tol > 0.0 && cyc == 0 && x0_zero) ? 1 : 0;
+    if (cyc == 0 && x0_zero)
+      launch_gs<R>(GS_SUB_STORE_NORM, nullptr, 0, 0, nullptr, b, bs, I.V, c.act, c.na, n, es, c.st);
+    else
+      launch_stencil<R>(op, c.slot_f, c.act, c.na, x, Scale<R>{}, b, bs, I.V, c.st, &es);
     if (tol > 0.0) {
       cudaMemcpyAsync(rn.data(), I.ks.rnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
       cudaMemcpyAsync(bn.data(), I.ks.bnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
@@ -288,29 +304,42 @@ static int krylov(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x
       if (keep.size() != c.act_h.size()) set_active(c, keep);
       if (c.na == 0) break;
     }
-    const bool flex = I.flex && prec;
+    const cplx<R>* coef = (const cplx<R>*)I.ks.coef;
     for (int j = 0; j < I.k; ++j) {
       cplx<R>* Vj = I.V + (size_t)j * vs;
+      const cplx<R>* zin = Vj;
+      Scale<R> zs{(const R*)I.ks.scale_r + j, K1};
       if (flex) {
         cplx<R>* Zj = I.Z + (size_t)j * vs;
-        (*prec)(Vj, Scale<R>{(const R*)I.ks.scale_r + j, K1}, Zj);
-        launch_stencil<R>(op, c.slot_f, c.act, c.na, Zj, Scale<R>{}, nullptr, Scale<R>{}, I.w, c.st);
-      } else {
-        launch_stencil<R>(op, c.slot_f, c.act, c.na, Vj, Scale<R>{(const R*)I.ks.scale_r + j, K1}, nullptr,
-                          Scale<R>{}, I.w, c.st);
+        (*prec)(Vj, zs, Zj);
+        zin = Zj;
+        zs = Scale<R>{};
       }
-      const cplx<R>* coef = (const cplx<R>*)I.ks.coef;
-      nb = launch_gs<R>(GS_DOT, I.V, vs, j + 1, nullptr, I.w, Scale<R>{}, nullptr, c.act, c.na, n, c.partial, c.st);
-      launch_red_dots(c.partial, nb, j + 1, c.act, c.na, I.ks, 0, rb, c.st);
-      nb = launch_gs<R>(GS_SUB_DOT, I.V, vs, j + 1, coef, I.w, Scale<R>{}, nullptr, c.act, c.na, n, c.partial, c.st);
-      launch_red_dots(c.partial, nb, j + 1, c.act, c.na, I.ks, 1, rb, c.st);
-      nb = launch_gs<R>(GS_SUB_STORE_NORM, I.V, vs, j + 1, coef, I.w, Scale<R>{}, I.V + (size_t)(j + 1) * vs,
-                        c.act, c.na, n, c.partial, c.st);
-      launch_red_norm_arnoldi(c.partial, nb, c.act, c.na, I.ks, j, rb, c.st);
+      // w = H z_j and the first Gram-Schmidt pass h = V^H w (folded into the
+      // stencil, or as a separate streaming pass)
+      Epi ed = make_epi(c, EPI_DOTS, &I.ks);
+      ed.nv = j + 1;
+      if (HELM_FUSE_DOTS) {
+        launch_stencil<R>(op, c.slot_f, c.act, c.na, zin, zs, nullptr, Scale<R>{}, I.w, c.st, &ed, I.V, vs, j + 1);
+      } else {
+        launch_stencil<R>(op, c.slot_f, c.act, c.na, zin, zs, nullptr, Scale<R>{}, I.w, c.st);
+        launch_gs<R>(GS_DOT, I.V, vs, j + 1, nullptr, I.w, Scale<R>{}, nullptr, c.act, c.na, n, ed, c.st);
+      }
+      if (reorth) {
+        Epi e2 = make_epi(c, EPI_DOTS, &I.ks);
+        e2.nv = j + 1;
+        e2.accumulate = 1;
+        launch_gs<R>(GS_SUB_DOT, I.V, vs, j + 1, coef, I.w, Scale<R>{}, nullptr, c.act, c.na, n, e2, c.st);
+      }
+      // v_{j+1} = w - V h, its norm, the Givens update (and the small solve after the last column)
+      Epi ea = make_epi(c, EPI_ARNOLDI, &I.ks);
+      ea.j = j;
+      ea.ksolve = I.k;
+      ea.flex = flex ? 1 : 0;
+      launch_gs<R>(GS_SUB_STORE_NORM, I.V, vs, j + 1, coef, I.w, Scale<R>{}, I.V + (size_t)(j + 1) * vs, c.act,
+                   c.na, n, ea, c.st);
     }
-    launch_small_solve(c.act, c.na, I.ks, I.k, flex ? 1 : 0, rb, c.st);
-    launch_gs<R>(GS_ADD_STORE, flex ? I.Z : I.V, vs, I.k, (const cplx<R>*)I.ks.coef, x, Scale<R>{}, x, c.act,
-                 c.na, n, c.partial, c.st);
+    launch_gs<R>(GS_ADD_STORE, flex ? I.Z : I.V, vs, I.k, coef, x, Scale<R>{}, x, c.act, c.na, n, Epi{}, c.st);
     if (out) {
       for (int s : c.act_h) out->iters[s] += I.k;
       out->cycles++;
@@ -319,12 +348,52 @@ static int krylov(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x
   if (tol > 0.0) {
     set_active(c, saved);
     if (final_resid) {
-      // final true residual for the caller's slots
-      launch_stencil<R>(op, c.slot_f, c.act, c.na, x, Scale<R>{}, b, bs, I.w, c.st);
-      norms<R>(c, I.w, Scale<R>{}, n, I.ks.rnorm);
+      // final true residual norm for the caller's slots
+      Epi en = make_epi(c, EPI_NORM);
+      en.out = I.ks.rnorm;
+      launch_stencil<R>(op, c.slot_f, c.act, c.na, x, Scale<R>{}, b, bs, I.w, c.st, &en);
     }
   }
   return status;
+}
+
+// s-step GMRES cycles (the same minimal-residual step as GMRES(k) from x, over
+// the same Krylov space): W_0 = r = bs*b - H x, W_i = H W_{i-1} for i = 1..k,
+// one Gram pass over W_0..W_k, the k x k normal equations in FP64 (diagonally
+// scaled, so the basis needs no normalisation), x += sum_i y_i W_i.  A cycle
+// streams k+3 passes instead of the ~k^2 of Gram-Schmidt.
+template <typename R>
+static void sstep(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero, int cycles) {
+  const OpView<R> op = op_view<R>(c, I.level, c.dir);
+  const size_t n = op.n;
+  const size_t vs = (size_t)c.B * n;
+  const int S = I.k;
+  for (int cyc = 0; cyc < cycles && c.na > 0; ++cyc) {
+    if (cyc == 0 && x0_zero) {
+      // x = 0: the residual is bs*b itself; the first image is H(bs*b)
+      launch_zero<R>(x, c.act, c.na, n, c.st);
+      launch_gs<R>(GS_ADD_STORE, nullptr, 0, 0, nullptr, b, bs, I.V, c.act, c.na, n, Epi{}, c.st);
+    } else {
+      launch_stencil<R>(op, c.slot_f, c.act, c.na, x, Scale<R>{}, b, bs, I.V, c.st);
+    }
+    for (int i = 1; i <= S; ++i)
+      launch_stencil<R>(op, c.slot_f, c.act, c.na, I.V + (size_t)(i - 1) * vs, Scale<R>{}, nullptr, Scale<R>{},
+                        I.V + (size_t)i * vs, c.st);
+    Epi eg = make_epi(c, EPI_GRAM, &I.ks);
+    eg.idx = S;
+    launch_gram<R>(I.V, vs, S, c.act, c.na, n, eg, c.st);
+    launch_gs<R>(GS_ADD_STORE, I.V, vs, S, (const cplx<R>*)I.ks.coef, x, Scale<R>{}, x, c.act, c.na, n, Epi{}, c.st);
+  }
+}
+
+// A fixed-cycle solve without preconditioner (smoother or last-level coarse
+// solve): s-step cycles when enabled, Arnoldi otherwise.
+template <typename R>
+static void fixed_solve(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero, int cycles) {
+  if (c.P->o.sstep && I.k <= SSTEP_MAX)
+    sstep<R>(c, I, b, bs, x, x0_zero, cycles);
+  else
+    krylov<R>(c, I, b, bs, x, x0_zero, cycles, 0.0, nullptr, nullptr);
 }
 
 // ML-GMRES V-cycle at `level`: out = M^{-1}(ins*in), zero initial guess.
@@ -337,7 +406,7 @@ static void vcycle(Ctx& c, int level, const cplx<R>* in, Scale<R> ins, cplx<R>* 
   KInst<R>& coarse = H.inst[level == 0 ? 2 : 4];
   const OpView<R> op = op_view<R>(c, level, c.dir);
   // pre-smoothing from zero
-  krylov<R>(c, smooth, in, ins, out, true, o.k_so, 0.0, nullptr, nullptr);
+  fixed_solve<R>(c, smooth, in, ins, out, true, o.k_so);
   // residual, restriction
   launch_stencil<R>(op, c.slot_f, c.act, c.na, out, Scale<R>{}, in, ins, H.r[level], c.st);
   launch_restrict<R>(H.r[level], P.lev[level], H.b[level + 1], P.lev[level + 1], c.act, c.na, c.st);
@@ -348,11 +417,11 @@ static void vcycle(Ctx& c, int level, const cplx<R>* in, Scale<R> ins, cplx<R>* 
     };
     krylov<R>(c, coarse, H.b[level + 1], Scale<R>{}, H.x[level + 1], true, o.k_co, 0.0, &pc, nullptr);
   } else {
-    krylov<R>(c, coarse, H.b[level + 1], Scale<R>{}, H.x[level + 1], true, o.k_co, 0.0, nullptr, nullptr);
+    fixed_solve<R>(c, coarse, H.b[level + 1], Scale<R>{}, H.x[level + 1], true, o.k_co);
   }
   launch_prolong_add<R>(H.x[level + 1], P.lev[level + 1], out, P.lev[level], c.act, c.na, c.st);
   // post-smoothing from the corrected guess
-  krylov<R>(c, smooth, in, ins, out, false, o.k_so, 0.0, nullptr, nullptr);
+  fixed_solve<R>(c, smooth, in, ins, out, false, o.k_so);
 }
 
 // Damped Jacobi: sweeps of z += omega D^{-1}(ins*in - H z), from z = 0.
@@ -422,13 +491,21 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
       }
       if (keep.size() != c.act_h.size()) set_active(c, keep);
       if (c.na == 0 || it == o.max_refine) break;
-      for (int s : c.act_h) rep[s].refine++;
+      // inner tolerance: the reduction the strictest active slot still needs
+      // (with a safety factor), but no tighter than tol_inner
+      double need = 1.0;
+      for (int s : c.act_h) {
+        rep[s].refine++;
+        need = std::min(need, o.tol * qn[s] / rn[s]);
+      }
+      const double itol = std::min(0.5, std::max(o.tol_inner, 0.5 * need));
       launch_to32_scaled(c.r64, c.nrm, c.b32, c.act, c.na, n, c.st);
-      int s2 = outer_solve<float>(c, c.b32, c.x32, o.tol_inner, &ko, false);
+      int s2 = outer_solve<float>(c, c.b32, c.x32, itol, &ko, false);
       if (s2 == HELM_E_NONFINITE) st = s2;
       launch_axpy_up(c.x32, c.nrm, u, c.act, c.na, n, c.st);
-      launch_stencil<double>(op64, c.slot_f, c.act, c.na, u, Scale<double>{}, q, Scale<double>{}, c.r64, c.st);
-      norms<double>(c, c.r64, Scale<double>{}, n, c.nrm);
+      Epi en = make_epi(c, EPI_NORM);
+      en.out = c.nrm;
+      launch_stencil<double>(op64, c.slot_f, c.act, c.na, u, Scale<double>{}, q, Scale<double>{}, c.r64, c.st, &en);
     }
   }
   if (sync_check(c) != HELM_OK) return HELM_E_CUDA;

@@ -62,6 +62,7 @@ struct Ctx {
   int* ident = nullptr;    // 0..B-1
   int* err = nullptr;      // [4] device error counters
   double* partial = nullptr;
+  unsigned* counter = nullptr;  // [B] arrival tickets of the fused reductions
   // FP64 fields
   double2* q = nullptr;    // right-hand side
   double2* u = nullptr;    // solution (forward field)

@@ -10,79 +10,214 @@
 // transposed, conjugated tables, so one kernel serves both directions.
 //
 // Layout: fields are x-fastest [Nz][Ny][Nx] per right-hand-side slot, slots
-// n apart.  Thread (ix, iy) marches over a run of z-planes and keeps the
-// z-1 / z / z+1 values in registers; x and y neighbours come through L1.
-#include "common.cuh"
+// n apart.  A tile is STPB consecutive (x, y) columns of a plane (flattened,
+// so no lanes idle at ragged row ends) by ZRUN planes; each thread marches its
+// column in z, keeps the z-1 / z / z+1 values in registers and issues the
+// loads of the next plane before computing the current one; x and y
+// neighbours come through L1.  Blocks loop over tiles so the number of blocks
+// per slot is bounded, which lets the kernel also reduce its output: dot
+// products with Krylov basis vectors (the first Gram-Schmidt pass of an
+// Arnoldi step) or the norm of a residual (reduce.cuh).
+#include "reduce.cuh"
 
 namespace helm {
 
 namespace {
 
-constexpr int SBX = 32;   // block extent along x (one warp: coalesced rows)
-constexpr int SBY = 4;    // block extent along y
-constexpr int ZRUN = 16;  // z-planes per thread
+constexpr int STPB = 128;  // threads per block = consecutive (x, y) columns of a plane
+constexpr int ZRUN = 16;   // z-planes per tile
 
+struct TileGeom {
+  int K0, K1, K2;
+  int nseg, nzc, ntiles;  // plane segments of STPB columns, z-chunks, tiles per slot
+  size_t n;
+  int Nmax;
+};
+
+// Plain apply (no reduction): one tile per block, grid (tiles, active slots).
 template <typename R, bool RESID>
-__global__ void __launch_bounds__(SBX * SBY)
-k_stencil(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss,
-          const cplx<R>* __restrict__ b, const R* __restrict__ bs, int bss,
-          cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab, const R* __restrict__ m,
-          const R* __restrict__ w2, const int* __restrict__ slot_f, const int* __restrict__ act,
-          int K0, int K1, int K2, size_t n, int Nmax, int nzc) {
+__global__ void __launch_bounds__(STPB, sizeof(R) == 4 ? 12 : 6)
+k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
+                const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
+                const R* __restrict__ m, const R* __restrict__ w2, const int* __restrict__ slot_f,
+                const int* __restrict__ act, TileGeom G) {
   using C = cplx<R>;
-  const int ix = blockIdx.x * SBX + threadIdx.x;
-  const int iy = blockIdx.y * SBY + threadIdx.y;
-  const int a = blockIdx.z / nzc;
-  const int zc = blockIdx.z - a * nzc;
-  if (ix >= K0 || iy >= K1) return;
-  const int s = act[a];
+  const int planei = G.K0 * G.K1;
+  const int seg = blockIdx.x % G.nseg;
+  const int zc = blockIdx.x / G.nseg;
+  const int p2 = seg * STPB + threadIdx.x;
+  if (p2 >= planei) return;
+  const int s = act[blockIdx.y];
   const int f = slot_f[s];
-  const C* T = tab + (size_t)f * 9 * Nmax;
-  const C xm = T[ix], xd = T[Nmax + ix], xp = T[2 * Nmax + ix];
-  const C ym = T[3 * Nmax + iy], yd = T[4 * Nmax + iy], yp = T[5 * Nmax + iy];
-  const C* Tz = T + 6 * Nmax;
+  const C* T = tab + (size_t)f * 9 * G.Nmax;
+  const C* Tz = T + 6 * G.Nmax;
   const R om2 = w2[f];
-  const R sx = xs ? xs[(size_t)s * xss] : R(1);
-  R sb = R(0);
-  if (RESID) sb = bs ? bs[(size_t)s * bss] : R(1);
-  const C* X = x + (size_t)s * n;
-  C* Y = y + (size_t)s * n;
-  const C* Bv = RESID ? b + (size_t)s * n : nullptr;
-  const size_t plane = (size_t)K0 * K1;
+  const C* X = x + (size_t)s * G.n;
+  C* Y = y + (size_t)s * G.n;
+  const int ix = p2 % G.K0;
+  const int iy = p2 / G.K0;
+  const C xm = T[ix], xd = T[G.Nmax + ix], xp = T[2 * G.Nmax + ix];
+  const C ym = T[3 * G.Nmax + iy], yd = T[4 * G.Nmax + iy], yp = T[5 * G.Nmax + iy];
+  const R dre = xd.x + yd.x, dim = xd.y + yd.y;
   const int z0 = zc * ZRUN;
-  const int z1 = min(z0 + ZRUN, K2);
-  size_t p = (size_t)ix + (size_t)K0 * iy + plane * z0;
+  const int z1 = min(z0 + ZRUN, G.K2);
+  const size_t plane = (size_t)planei;
+  size_t p = (size_t)p2 + plane * z0;
   const C zero = mkc(R(0), R(0));
-  const bool hw = ix > 0, he = ix + 1 < K0, hs = iy > 0, hn = iy + 1 < K1;
+  const bool hw = ix > 0, he = ix + 1 < G.K0, hs = iy > 0, hn = iy + 1 < G.K1;
   C prev = z0 > 0 ? X[p - plane] : zero;
   C cur = X[p];
-  const R dxy_re = xd.x + yd.x, dxy_im = xd.y + yd.y;
+  C next = (z0 + 1 < G.K2) ? X[p + plane] : zero;
+  C w = hw ? X[p - 1] : zero, ea = he ? X[p + 1] : zero, so = hs ? X[p - G.K0] : zero, no = hn ? X[p + G.K0] : zero;
+  R mm = m[p];
   for (int z = z0; z < z1; ++z, p += plane) {
-    const C next = (z + 1 < K2) ? X[p + plane] : zero;
-    const C w = hw ? X[p - 1] : zero;
-    const C e = he ? X[p + 1] : zero;
-    const C so = hs ? X[p - K0] : zero;
-    const C no = hn ? X[p + K0] : zero;
-    const C zm = Tz[z], zd = Tz[Nmax + z], zp = Tz[2 * Nmax + z];
-    const C diag = mkc(dxy_re + zd.x + om2 * m[p], dxy_im + zd.y);
-    C acc = cmul(diag, cur);
-    acc = cfma(xm, w, acc);
-    acc = cfma(xp, e, acc);
-    acc = cfma(ym, so, acc);
-    acc = cfma(yp, no, acc);
-    acc = cfma(zm, prev, acc);
-    acc = cfma(zp, next, acc);
-    C out;
-    if (RESID) {
-      const C bv = Bv ? Bv[p] : zero;
-      out = mkc(sb * bv.x - sx * acc.x, sb * bv.y - sx * acc.y);
-    } else {
-      out = mkc(sx * acc.x, sx * acc.y);
+    const size_t q = p + plane;
+    const bool more = z + 1 < z1;
+    C next2 = zero, w2n = zero, e2n = zero, s2n = zero, n2n = zero;
+    R m2 = R(0);
+    if (more) {
+      next2 = (z + 2 < G.K2) ? X[q + plane] : zero;
+      w2n = hw ? X[q - 1] : zero;
+      e2n = he ? X[q + 1] : zero;
+      s2n = hs ? X[q - G.K0] : zero;
+      n2n = hn ? X[q + G.K0] : zero;
+      m2 = m[q];
     }
-    Y[p] = out;
+    const C zm = Tz[z], zd = Tz[G.Nmax + z], zp = Tz[2 * G.Nmax + z];
+    const C diag = mkc(dre + zd.x + om2 * mm, dim + zd.y);
+    C h = cmul(diag, cur);
+    h = cfma(xm, w, h);
+    h = cfma(xp, ea, h);
+    h = cfma(ym, so, h);
+    h = cfma(yp, no, h);
+    h = cfma(zm, prev, h);
+    h = cfma(zp, next, h);
+    if (RESID) {
+      const R sx = xs ? xs[(size_t)s * xss] : R(1);
+      const R sb = bs ? bs[(size_t)s * bss] : R(1);
+      const C bv = b[(size_t)s * G.n + (p - 0)];
+      Y[p] = mkc(sb * bv.x - sx * h.x, sb * bv.y - sx * h.y);
+    } else if (xs) {
+      const R sx = xs[(size_t)s * xss];
+      Y[p] = mkc(sx * h.x, sx * h.y);
+    } else {
+      Y[p] = h;
+    }
     prev = cur;
     cur = next;
+    next = next2;
+    w = w2n;
+    ea = e2n;
+    so = s2n;
+    no = n2n;
+    mm = m2;
   }
+}
+
+// RED: 0 no reduction, -1 norm of the output, KM > 0 dots of the output with up to KM basis vectors
+template <typename R, bool RESID, int RED>
+__global__ void __launch_bounds__(STPB)
+k_stencil(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
+          const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
+          const R* __restrict__ m, const R* __restrict__ w2, const int* __restrict__ slot_f,
+          const int* __restrict__ act, TileGeom G, const cplx<R>* __restrict__ V, size_t vstride, int nv, Epi e) {
+  using C = cplx<R>;
+  constexpr int KM = RED > 0 ? RED : 1;
+  constexpr int NVAL = RED > 0 ? 2 * RED : 1;
+  const int a = blockIdx.y;
+  const int s = act[a];
+  const int f = slot_f[s];
+  const C* T = tab + (size_t)f * 9 * G.Nmax;
+  const C* Tz = T + 6 * G.Nmax;
+  const R om2 = w2[f];
+  const R sx = xs ? xs[(size_t)s * xss] : R(1);
+  const R sb = (RESID && bs) ? bs[(size_t)s * bss] : R(1);
+  const C* X = x + (size_t)s * G.n;
+  C* Y = y + (size_t)s * G.n;
+  const C* Bv = RESID ? b + (size_t)s * G.n : nullptr;
+  const C* Vs = RED > 0 ? V + (size_t)s * G.n : nullptr;
+  const size_t plane = (size_t)G.K0 * G.K1;
+  const C zero = mkc(R(0), R(0));
+  R acc[NVAL];
+#pragma unroll
+  for (int k = 0; k < NVAL; ++k) acc[k] = R(0);
+  const int planei = G.K0 * G.K1;
+  for (int tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
+    const int seg = tile % G.nseg;
+    const int zc = tile / G.nseg;
+    const int p2 = seg * STPB + threadIdx.x;
+    if (p2 >= planei) continue;
+    const int ix = p2 % G.K0;
+    const int iy = p2 / G.K0;
+    const C xm = T[ix], xd = T[G.Nmax + ix], xp = T[2 * G.Nmax + ix];
+    const C ym = T[3 * G.Nmax + iy], yd = T[4 * G.Nmax + iy], yp = T[5 * G.Nmax + iy];
+    const R dxy_re = xd.x + yd.x, dxy_im = xd.y + yd.y;
+    const int z0 = zc * ZRUN;
+    const int z1 = min(z0 + ZRUN, G.K2);
+    const bool hw = ix > 0, he = ix + 1 < G.K0, hs = iy > 0, hn = iy + 1 < G.K1;
+    size_t p = (size_t)p2 + plane * z0;
+    // register pipeline: the loads of plane z+1 are issued before plane z is computed
+    C prev = z0 > 0 ? X[p - plane] : zero;
+    C cur = X[p];
+    C next = (z0 + 1 < G.K2) ? X[p + plane] : zero;
+    C w = hw ? X[p - 1] : zero, ea = he ? X[p + 1] : zero;
+    C so = hs ? X[p - G.K0] : zero, no = hn ? X[p + G.K0] : zero;
+    R mm = m[p];
+    for (int z = z0; z < z1; ++z, p += plane) {
+      const size_t q = p + plane;
+      const bool more = z + 1 < z1;
+      C next2 = zero, w2n = zero, e2n = zero, s2n = zero, n2n = zero;
+      R m2 = R(0);
+      if (more) {
+        next2 = (z + 2 < G.K2) ? X[q + plane] : zero;
+        w2n = hw ? X[q - 1] : zero;
+        e2n = he ? X[q + 1] : zero;
+        s2n = hs ? X[q - G.K0] : zero;
+        n2n = hn ? X[q + G.K0] : zero;
+        m2 = m[q];
+      }
+      const C zm = Tz[z], zd = Tz[G.Nmax + z], zp = Tz[2 * G.Nmax + z];
+      const C diag = mkc(dxy_re + zd.x + om2 * mm, dxy_im + zd.y);
+      C h = cmul(diag, cur);
+      h = cfma(xm, w, h);
+      h = cfma(xp, ea, h);
+      h = cfma(ym, so, h);
+      h = cfma(yp, no, h);
+      h = cfma(zm, prev, h);
+      h = cfma(zp, next, h);
+      C out;
+      if (RESID) {
+        const C bv = Bv[p];
+        out = mkc(sb * bv.x - sx * h.x, sb * bv.y - sx * h.y);
+      } else {
+        out = mkc(sx * h.x, sx * h.y);
+      }
+      Y[p] = out;
+      if (RED < 0) acc[0] = fma(out.x, out.x, fma(out.y, out.y, acc[0]));
+      if (RED > 0) {
+#pragma unroll
+        for (int i = 0; i < KM; ++i) {
+          if (i < nv) {
+            const C v = Vs[i * vstride + p];
+            acc[2 * i] = fma(v.x, out.x, fma(v.y, out.y, acc[2 * i]));
+            acc[2 * i + 1] = fma(v.x, out.y, fma(-v.y, out.x, acc[2 * i + 1]));
+          }
+        }
+      }
+      prev = cur;
+      cur = next;
+      next = next2;
+      w = w2n;
+      ea = e2n;
+      so = s2n;
+      no = n2n;
+      mm = m2;
+    }
+  }
+  if (RED == 0) return;
+  const int nvals = RED > 0 ? 2 * nv : 1;
+  block_partial_row<R, NVAL>(acc, nvals, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * nvals);
+  epi_arrive<R>(e, a, s, gridDim.x, nvals);
 }
 
 // Diagonal of H at p: sum of the three cd tables and w^2 m.
@@ -102,10 +237,9 @@ __device__ __forceinline__ cplx<R> cdiv(cplx<R> a, cplx<R> d) {
 // z = omega D^{-1} (bs * b): the first damped-Jacobi sweep from a zero guess.
 template <typename R>
 __global__ void k_jacobi_first(const cplx<R>* __restrict__ b, const R* __restrict__ bs, int bss,
-                               cplx<R>* __restrict__ z, const cplx<R>* __restrict__ tab,
-                               const R* __restrict__ m, const R* __restrict__ w2,
-                               const int* __restrict__ slot_f, const int* __restrict__ act, int K0,
-                               int K1, int K2, size_t n, int Nmax, R omega) {
+                               cplx<R>* __restrict__ z, const cplx<R>* __restrict__ tab, const R* __restrict__ m,
+                               const R* __restrict__ w2, const int* __restrict__ slot_f,
+                               const int* __restrict__ act, int K0, int K1, int K2, size_t n, int Nmax, R omega) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int s = act[blockIdx.y];
@@ -117,17 +251,15 @@ __global__ void k_jacobi_first(const cplx<R>* __restrict__ b, const R* __restric
   const cplx<R> d = diag_at<R>(T, Nmax, ix, iy, iz, w2[f], m[i]);
   const R sb = bs ? bs[(size_t)s * bss] : R(1);
   const cplx<R> bv = b[(size_t)s * n + i];
-  const cplx<R> q = cdiv<R>(mkc(omega * sb * bv.x, omega * sb * bv.y), d);
-  z[(size_t)s * n + i] = q;
+  z[(size_t)s * n + i] = cdiv<R>(mkc(omega * sb * bv.x, omega * sb * bv.y), d);
 }
 
 // z += omega D^{-1} r
 template <typename R>
 __global__ void k_jacobi_update(const cplx<R>* __restrict__ r, cplx<R>* __restrict__ z,
-                                const cplx<R>* __restrict__ tab, const R* __restrict__ m,
-                                const R* __restrict__ w2, const int* __restrict__ slot_f,
-                                const int* __restrict__ act, int K0, int K1, int K2, size_t n,
-                                int Nmax, R omega) {
+                                const cplx<R>* __restrict__ tab, const R* __restrict__ m, const R* __restrict__ w2,
+                                const int* __restrict__ slot_f, const int* __restrict__ act, int K0, int K1, int K2,
+                                size_t n, int Nmax, R omega) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int s = act[blockIdx.y];
@@ -139,63 +271,110 @@ __global__ void k_jacobi_update(const cplx<R>* __restrict__ r, cplx<R>* __restri
   const cplx<R> d = diag_at<R>(T, Nmax, ix, iy, iz, w2[f], m[i]);
   const cplx<R> rv = r[(size_t)s * n + i];
   const cplx<R> q = cdiv<R>(mkc(omega * rv.x, omega * rv.y), d);
-  cplx<R> zv = z[(size_t)s * n + i];
+  const cplx<R> zv = z[(size_t)s * n + i];
   z[(size_t)s * n + i] = mkc(zv.x + q.x, zv.y + q.y);
+}
+
+template <typename R, bool RESID, int RED>
+void stencil_go(dim3 grd, cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act,
+                const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y, const TileGeom& G,
+                const cplx<R>* V, size_t vstride, int nv, const Epi& e) {
+  k_stencil<R, RESID, RED><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
+                                                          op.w2, slot_f, act, G, V, vstride, nv, e);
+}
+
+template <typename R, bool RESID>
+void stencil_red(dim3 grd, cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act,
+                 const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y, const TileGeom& G,
+                 const cplx<R>* V, size_t vstride, int nv, const Epi& e) {
+  if (e.kind == EPI_NONE)
+    stencil_go<R, RESID, 0>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
+  else if (e.kind != EPI_DOTS)
+    stencil_go<R, RESID, -1>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
+  else if (nv <= 4)
+    stencil_go<R, RESID, 4>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
+  else if (nv <= 8)
+    stencil_go<R, RESID, 8>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
+  else if (nv <= 16)
+    stencil_go<R, RESID, 16>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
+  else
+    stencil_go<R, RESID, KMAX + 1>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
 }
 
 }  // namespace
 
 template <typename R>
-void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int na,
-                    const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y,
-                    cudaStream_t st) {
+void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* x,
+                    Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y, cudaStream_t st, const Epi* epi,
+                    const cplx<R>* V, size_t vstride, int nv) {
   if (na <= 0) return;
-  const double by = (double)na * op.n * ((b || bs.p) ? 3 : 2) * sizeof(cplx<R>) + (double)op.n * sizeof(R);
+  Epi e = epi ? *epi : Epi{};
+  double by = (double)na * op.n * (b ? 3 : 2) * sizeof(cplx<R>) + (double)op.n * sizeof(R);
+  if (e.kind == EPI_DOTS) by += (double)na * op.n * nv * sizeof(cplx<R>);
   ProfScope ps(sizeof(R) == 4 ? PC_STENCIL32 : PC_STENCIL64, by, st);
-  const int nzc = (op.K[2] + ZRUN - 1) / ZRUN;
-  dim3 blk(SBX, SBY);
-  dim3 grd((op.K[0] + SBX - 1) / SBX, (op.K[1] + SBY - 1) / SBY, nzc * na);
-  if (b || bs.p) {
-    k_stencil<R, true><<<grd, blk, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
-                                            op.w2, slot_f, act, op.K[0], op.K[1], op.K[2], op.n,
-                                            op.Nmax, nzc);
+  TileGeom G;
+  G.K0 = op.K[0];
+  G.K1 = op.K[1];
+  G.K2 = op.K[2];
+  G.nseg = (int)(((size_t)G.K0 * G.K1 + STPB - 1) / STPB);
+  G.nzc = (G.K2 + ZRUN - 1) / ZRUN;
+  G.ntiles = G.nseg * G.nzc;
+  G.n = op.n;
+  G.Nmax = op.Nmax;
+  int nblk = G.ntiles;
+  if (e.kind != EPI_NONE) {
+    // bounded blocks per slot: every block reduces into one partial row
+    const int target = (152 * 12 + na - 1) / na;
+    nblk = std::min(G.ntiles, std::max(1, target));
+    const int rows = std::max(RED_BLOCKS_MAX, na);
+    if ((long long)nblk * na > rows) nblk = std::max(1, rows / na);
+  }
+  dim3 grd(nblk, na);
+  if (e.kind == EPI_NONE) {
+    if (b)
+      k_stencil_plain<R, true><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m, op.w2,
+                                                     slot_f, act, G);
+    else
+      k_stencil_plain<R, false><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m, op.w2,
+                                                      slot_f, act, G);
+  } else if (b) {
+    stencil_red<R, true>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
   } else {
-    k_stencil<R, false><<<grd, blk, 0, st>>>(x, xs.p, xs.stride, nullptr, nullptr, 0, y, op.tab, op.m,
-                                             op.w2, slot_f, act, op.K[0], op.K[1], op.K[2], op.n,
-                                             op.Nmax, nzc);
+    stencil_red<R, false>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
   }
   count_launch();
 }
 
 template <typename R>
-void launch_jacobi_first(const OpView<R>& op, const int* slot_f, const int* act, int na,
-                         const cplx<R>* b, Scale<R> bs, R omega, cplx<R>* z, cudaStream_t st) {
+void launch_jacobi_first(const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* b,
+                         Scale<R> bs, R omega, cplx<R>* z, cudaStream_t st) {
   if (na <= 0) return;
   ProfScope ps(PC_MISC, (double)na * op.n * 2 * sizeof(cplx<R>), st);
   dim3 grd((unsigned)((op.n + 255) / 256), na);
-  k_jacobi_first<R><<<grd, 256, 0, st>>>(b, bs.p, bs.stride, z, op.tab, op.m, op.w2, slot_f, act,
-                                         op.K[0], op.K[1], op.K[2], op.n, op.Nmax, omega);
+  k_jacobi_first<R><<<grd, 256, 0, st>>>(b, bs.p, bs.stride, z, op.tab, op.m, op.w2, slot_f, act, op.K[0], op.K[1],
+                                         op.K[2], op.n, op.Nmax, omega);
   count_launch();
 }
 
 template <typename R>
-void launch_jacobi_update(const OpView<R>& op, const int* slot_f, const int* act, int na,
-                          const cplx<R>* r, R omega, cplx<R>* z, cudaStream_t st) {
+void launch_jacobi_update(const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* r,
+                          R omega, cplx<R>* z, cudaStream_t st) {
   if (na <= 0) return;
   ProfScope ps(PC_MISC, (double)na * op.n * 3 * sizeof(cplx<R>), st);
   dim3 grd((unsigned)((op.n + 255) / 256), na);
-  k_jacobi_update<R><<<grd, 256, 0, st>>>(r, z, op.tab, op.m, op.w2, slot_f, act, op.K[0], op.K[1],
-                                          op.K[2], op.n, op.Nmax, omega);
+  k_jacobi_update<R><<<grd, 256, 0, st>>>(r, z, op.tab, op.m, op.w2, slot_f, act, op.K[0], op.K[1], op.K[2], op.n,
+                                          op.Nmax, omega);
   count_launch();
 }
 
-#define INST(R)                                                                                      \
-  template void launch_stencil<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*,     \
-                                  Scale<R>, const cplx<R>*, Scale<R>, cplx<R>*, cudaStream_t);       \
-  template void launch_jacobi_first<R>(const OpView<R>&, const int*, const int*, int,               \
-                                       const cplx<R>*, Scale<R>, R, cplx<R>*, cudaStream_t);        \
-  template void launch_jacobi_update<R>(const OpView<R>&, const int*, const int*, int,              \
-                                        const cplx<R>*, R, cplx<R>*, cudaStream_t);
+#define INST(R)                                                                                                 \
+  template void launch_stencil<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*, Scale<R>,      \
+                                  const cplx<R>*, Scale<R>, cplx<R>*, cudaStream_t, const Epi*, const cplx<R>*, \
+                                  size_t, int);                                                                 \
+  template void launch_jacobi_first<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*, Scale<R>, \
+                                       R, cplx<R>*, cudaStream_t);                                              \
+  template void launch_jacobi_update<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*, R,        \
+                                        cplx<R>*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -37,7 +37,8 @@ class HelmSolveOpts(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("tol", ctypes.c_double), ("tol_inner", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("k_so", ctypes.c_int), ("k_si", ctypes.c_int),
                 ("k_co", ctypes.c_int), ("k_ci", ctypes.c_int), ("jacobi_omega", ctypes.c_double),
-                ("jacobi_sweeps", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("jacobi_sweeps", ctypes.c_int), ("max_batch", ctypes.c_int), ("reorth", ctypes.c_int),
+                ("sstep", ctypes.c_int)]
 
 
 class HelmRhsReport(ctypes.Structure):

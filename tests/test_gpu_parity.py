@@ -109,6 +109,8 @@ OPTS = {
     "fp64-none": dict(precision=0, precond=0, k_inner=30, tol=1e-14, max_cycles=2000),
     "fp64-jacobi": dict(precision=0, precond=1, k_inner=20, tol=1e-14, max_cycles=2000, jacobi_sweeps=2),
     "mixed-mlgmres": dict(precision=1, precond=2, tol=1e-11),
+    "mixed-mlgmres-arnoldi-smoother": dict(precision=1, precond=2, tol=1e-11, sstep=0, reorth=0),
+    "fp64-mlgmres-arnoldi-smoother": dict(precision=0, precond=2, tol=1e-14, sstep=0),
     "mixed-none": dict(precision=1, precond=0, k_inner=30, tol=1e-11, max_cycles=400),
 }
 
