@@ -44,12 +44,12 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--precond", default="mlgmres", choices=["mlgmres", "jacobi", "none"])
     p.add_argument("--levels", type=int, default=2)
-    p.add_argument("--tol", type=float, default=1e-10)
-    p.add_argument("--tol-inner", type=float, default=1e-4)
-    p.add_argument("--k-inner", type=int, default=0, help="outer FGMRES cycle length (0: 5 with ML-GMRES, else 30)")
+    p.add_argument("--tol", type=float, default=1e-9)
+    p.add_argument("--tol-inner", type=float, default=0.1)
+    p.add_argument("--k-inner", type=int, default=0, help="outer FGMRES cycle length (0: 10 with ML-GMRES, else 30)")
     p.add_argument("--reorth", type=int, default=1)
     p.add_argument("--max-batch", type=int, default=0, help="right-hand sides solved together (0 = all)")
-    p.add_argument("--smoother", default="3,5,3,5", help="ML-GMRES (k_so, k_si, k_co, k_ci)")
+    p.add_argument("--smoother", default="3,6,3,6", help="ML-GMRES (k_so, k_si, k_co, k_ci)")
     p.add_argument("--n", type=int, default=64)
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -151,8 +151,19 @@ def cpu_baseline(n, seconds):
     per_pair_iters = iters["forward_iterations"] + iters["adjoint_iterations"]
     procs = max(1, min(os.cpu_count() or 1, 16))
     ctx = mp.get_context("spawn")
-    with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_worker, [(n, seconds, i) for i in range(procs)])
+    # one BLAS thread per spawned process (set before the children import numpy)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [(n, seconds, i) for i in range(procs)])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     t_iter = float(np.mean([r["seconds"] / r["iters"] for r in res]))
     pair_seconds = per_pair_iters * t_iter
     value = procs / pair_seconds
@@ -253,7 +264,7 @@ def main():
     levels = args.levels if args.precond == "mlgmres" else max(1, args.levels)
     grid = helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=levels)
     prec = {"mlgmres": helm.PRECOND_MLGMRES, "jacobi": helm.PRECOND_JACOBI, "none": helm.PRECOND_NONE}[args.precond]
-    kin = args.k_inner or (5 if prec == helm.PRECOND_MLGMRES else 30)
+    kin = args.k_inner or (10 if prec == helm.PRECOND_MLGMRES else 30)
     kso, ksi, kco, kci = (int(v) for v in args.smoother.split(","))
     opts = helm.default_opts(precision=helm.MIXED if args.precision == "mixed" else helm.FP64, precond=prec,
                              k_inner=kin, tol=args.tol, max_cycles=400, tol_inner=args.tol_inner, max_refine=60,

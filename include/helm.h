@@ -117,8 +117,10 @@ typedef struct {
 
 typedef struct helm_plan helm_plan;
 
-/* Fill `opts` with the defaults: MIXED, ML-GMRES (3,5,3,5), FGMRES(5),
- * tol 1e-10, tol_inner 1e-4, CGS2.  Returns HELM_OK. */
+/* Fill `opts` with the defaults: MIXED, ML-GMRES (3,5,3,5) with s-step
+ * smoothers, outer FGMRES(10) with CGS2, tol 1e-10, tol_inner 0.1 (about one
+ * complex64 FGMRES cycle per FP64 refinement step), max_refine 60.
+ * Returns HELM_OK. */
 int helm_default_opts(helm_solve_opts* opts);
 
 /* Validate `grid` and `opts` and build a host-side plan (no device memory).
@@ -226,7 +228,9 @@ typedef enum {
   HELM_PROF_TRANSFER = 5,     /* restriction / prolongation */
   HELM_PROF_FWI = 6,          /* sources, receivers, misfit, gradient, extension */
   HELM_PROF_MISC = 7,         /* conversions, zero fills, Jacobi */
-  HELM_PROF_NCLASS = 8
+  HELM_PROF_STENCIL_C64_COARSE = 8, /* complex64 stencil launches on grids below 200000 nodes */
+  HELM_PROF_KRYLOV_C64_COARSE = 9,  /* complex64 vector passes on grids below 200000 nodes */
+  HELM_PROF_NCLASS = 10
 } helm_prof_class;
 int helm_profile_enable(int on);
 int helm_profile_read(int cls, uint64_t* launches, double* ms, double* bytes);

@@ -199,11 +199,11 @@ int helm_default_opts(helm_solve_opts* o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = HELM_MIXED;
   o->precond = HELM_PRECOND_MLGMRES;
-  o->k_inner = 5;
+  o->k_inner = 10;
   o->max_cycles = 200;
   o->tol = 1e-10;
-  o->tol_inner = 1e-4;
-  o->max_refine = 12;
+  o->tol_inner = 0.1;
+  o->max_refine = 60;
   o->k_so = 3;
   o->k_si = 5;
   o->k_co = 3;

@@ -62,8 +62,17 @@ inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_o
 // launch in a class is bracketed by CUDA events on its stream and its
 // algorithmic bytes are accumulated.
 enum ProfClass {
-  PC_STENCIL32 = 0, PC_STENCIL64, PC_GS32, PC_GS64, PC_SMALL, PC_TRANSFER, PC_FWI, PC_MISC, PC_COUNT
+  PC_STENCIL32 = 0, PC_STENCIL64, PC_GS32, PC_GS64, PC_SMALL, PC_TRANSFER, PC_FWI, PC_MISC,
+  PC_STENCIL32_COARSE, PC_GS32_COARSE, PC_COUNT
 };
+// Launches on grids below this many nodes per field are booked to the coarse classes.
+constexpr size_t PROF_COARSE_N = 200000;
+template <typename R> inline int prof_stencil_class(size_t n) {
+  return sizeof(R) == 8 ? PC_STENCIL64 : (n < PROF_COARSE_N ? PC_STENCIL32_COARSE : PC_STENCIL32);
+}
+template <typename R> inline int prof_gs_class(size_t n) {
+  return sizeof(R) == 8 ? PC_GS64 : (n < PROF_COARSE_N ? PC_GS32_COARSE : PC_GS32);
+}
 struct ProfScope {
   ProfScope(int cls, double bytes, cudaStream_t st);
   ~ProfScope();

@@ -73,7 +73,7 @@ k_gs(const cplx<R>* __restrict__ V, size_t vstride, int nv, const cplx<R>* __res
   }
   if (MODE == GS_ADD_STORE || e.kind == EPI_NONE) return;
   const int nvals = DOTS ? 2 * nv : 1;
-  block_partial_row<R, NVAL>(acc, nvals, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * nvals);
+  block_partial_row<R, NVAL, GS_THREADS / 32>(acc, nvals, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * nvals);
   epi_arrive<R>(e, a, s, gridDim.x, nvals);
 }
 
@@ -101,7 +101,7 @@ void gs_pick(int nv, dim3 grd, cudaStream_t st, const cplx<R>* V, size_t vstride
 // Gram pass of an s-step cycle: raw <W_i, W_j> (1 <= i <= j <= S) and
 // <W_i, W_0> over the stored basis W_0..W_S, folded into EPI_GRAM.
 template <typename R, int S>
-__global__ void __launch_bounds__(GS_THREADS)
+__global__ void __launch_bounds__(GS_THREADS, sizeof(R) == 4 ? 3 : 2)
 k_gram(const cplx<R>* __restrict__ V, size_t vstride, const int* __restrict__ act, size_t n, size_t chunk, Epi e) {
   using C = cplx<R>;
   constexpr int NV = gram_nvals(S);
@@ -133,7 +133,7 @@ k_gram(const cplx<R>* __restrict__ V, size_t vstride, const int* __restrict__ ac
     }
     acc[2 * k] = fma(w[0].x, w[0].x, fma(w[0].y, w[0].y, acc[2 * k]));
   }
-  block_partial_row<R, NV>(acc, NV, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * NV);
+  block_partial_row<R, NV, GS_THREADS / 32>(acc, NV, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * NV);
   epi_arrive<R>(e, a, s, gridDim.x, NV);
 }
 
@@ -196,7 +196,7 @@ void launch_gs(int mode, const cplx<R>* V, size_t vstride, int nv, const cplx<R>
   double vecs = nv + 1;                             // V_0..V_{nv-1} and w read once
   if (mode == GS_SUB_STORE_NORM && out) vecs += 1;  // plus the stored result
   if (mode == GS_ADD_STORE) vecs += 1;              // x read and written
-  ProfScope ps(sizeof(R) == 4 ? PC_GS32 : PC_GS64, vecs * na * n * sizeof(cplx<R>), st);
+  ProfScope ps(prof_gs_class<R>(n), vecs * na * n * sizeof(cplx<R>), st);
   switch (mode) {
     case GS_DOT: gs_pick<R, GS_DOT>(nv, grd, st, V, vstride, coef, w, ws, out, act, n, chunk, e); break;
     case GS_SUB_DOT: gs_pick<R, GS_SUB_DOT>(nv, grd, st, V, vstride, coef, w, ws, out, act, n, chunk, e); break;
@@ -215,7 +215,7 @@ void launch_gram(const cplx<R>* V, size_t vstride, int s, const int* act, int na
   const int nblk = reduction_blocks(na, n, GS_THREADS);
   const size_t chunk = (n + nblk - 1) / nblk;
   dim3 grd(nblk, na);
-  ProfScope ps(sizeof(R) == 4 ? PC_GS32 : PC_GS64, (double)(s + 1) * na * n * sizeof(cplx<R>), st);
+  ProfScope ps(prof_gs_class<R>(n), (double)(s + 1) * na * n * sizeof(cplx<R>), st);
   switch (s) {
     case 1: gram_go<R, 1>(grd, st, V, vstride, act, n, chunk, e); break;
     case 2: gram_go<R, 2>(grd, st, V, vstride, act, n, chunk, e); break;

@@ -45,9 +45,8 @@ __device__ __forceinline__ R warp_sum(R v) {
 
 // Block-reduce vals[0..nvals) (every thread of the block calls this) and write
 // the block's partial row.
-template <typename R, int NV>
+template <typename R, int NV, int MAXW>
 __device__ __forceinline__ void block_partial_row(R (&vals)[NV], int nvals, double* row) {
-  constexpr int MAXW = 32;
   __shared__ double sh[MAXW][NV];
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;

@@ -36,7 +36,7 @@ struct TileGeom {
 
 // Plain apply (no reduction): one tile per block, grid (tiles, active slots).
 template <typename R, bool RESID>
-__global__ void __launch_bounds__(STPB, sizeof(R) == 4 ? 12 : 6)
+__global__ void __launch_bounds__(STPB, sizeof(R) == 4 ? 10 : 6)
 k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
                 const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
                 const R* __restrict__ m, const R* __restrict__ w2, const int* __restrict__ slot_f,
@@ -61,27 +61,35 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
   const R dre = xd.x + yd.x, dim = xd.y + yd.y;
   const int z0 = zc * ZRUN;
   const int z1 = min(z0 + ZRUN, G.K2);
-  const size_t plane = (size_t)planei;
-  size_t p = (size_t)p2 + plane * z0;
+  // pointer stepping: xq/yq/mq address plane z of this column; neighbours are
+  // fixed offsets from xq
+  const int P = planei;
+  const int K0 = G.K0;
+  const size_t p0 = (size_t)p2 + (size_t)P * z0;
+  const C* xq = X + p0;
+  C* yq = Y + p0;
+  const R* mq = m + p0;
+  const C* bq = RESID ? b + (size_t)s * G.n + p0 : nullptr;
+  const R sx = xs ? xs[(size_t)s * xss] : R(1);
+  const R sb = (RESID && bs) ? bs[(size_t)s * bss] : R(1);
   const C zero = mkc(R(0), R(0));
-  const bool hw = ix > 0, he = ix + 1 < G.K0, hs = iy > 0, hn = iy + 1 < G.K1;
-  C prev = z0 > 0 ? X[p - plane] : zero;
-  C cur = X[p];
-  C next = (z0 + 1 < G.K2) ? X[p + plane] : zero;
-  C w = hw ? X[p - 1] : zero, ea = he ? X[p + 1] : zero, so = hs ? X[p - G.K0] : zero, no = hn ? X[p + G.K0] : zero;
-  R mm = m[p];
-  for (int z = z0; z < z1; ++z, p += plane) {
-    const size_t q = p + plane;
-    const bool more = z + 1 < z1;
+  const bool hw = ix > 0, he = ix + 1 < K0, hs = iy > 0, hn = iy + 1 < G.K1;
+  C prev = z0 > 0 ? xq[-P] : zero;
+  C cur = xq[0];
+  C next = (z0 + 1 < G.K2) ? xq[P] : zero;
+  C w = hw ? xq[-1] : zero, ea = he ? xq[1] : zero, so = hs ? xq[-K0] : zero, no = hn ? xq[K0] : zero;
+  R mm = mq[0];
+  for (int z = z0; z < z1; ++z) {
+    const C* xn = xq + P;  // plane z+1
     C next2 = zero, w2n = zero, e2n = zero, s2n = zero, n2n = zero;
     R m2 = R(0);
-    if (more) {
-      next2 = (z + 2 < G.K2) ? X[q + plane] : zero;
-      w2n = hw ? X[q - 1] : zero;
-      e2n = he ? X[q + 1] : zero;
-      s2n = hs ? X[q - G.K0] : zero;
-      n2n = hn ? X[q + G.K0] : zero;
-      m2 = m[q];
+    if (z + 1 < z1) {
+      next2 = (z + 2 < G.K2) ? xn[P] : zero;
+      w2n = hw ? xn[-1] : zero;
+      e2n = he ? xn[1] : zero;
+      s2n = hs ? xn[-K0] : zero;
+      n2n = hn ? xn[K0] : zero;
+      m2 = mq[P];
     }
     const C zm = Tz[z], zd = Tz[G.Nmax + z], zp = Tz[2 * G.Nmax + z];
     const C diag = mkc(dre + zd.x + om2 * mm, dim + zd.y);
@@ -93,16 +101,15 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
     h = cfma(zm, prev, h);
     h = cfma(zp, next, h);
     if (RESID) {
-      const R sx = xs ? xs[(size_t)s * xss] : R(1);
-      const R sb = bs ? bs[(size_t)s * bss] : R(1);
-      const C bv = b[(size_t)s * G.n + (p - 0)];
-      Y[p] = mkc(sb * bv.x - sx * h.x, sb * bv.y - sx * h.y);
-    } else if (xs) {
-      const R sx = xs[(size_t)s * xss];
-      Y[p] = mkc(sx * h.x, sx * h.y);
+      const C bv = bq[0];
+      yq[0] = mkc(sb * bv.x - sx * h.x, sb * bv.y - sx * h.y);
+      bq += P;
     } else {
-      Y[p] = h;
+      yq[0] = mkc(sx * h.x, sx * h.y);
     }
+    xq = xn;
+    yq += P;
+    mq += P;
     prev = cur;
     cur = next;
     next = next2;
@@ -216,7 +223,7 @@ k_stencil(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, cons
   }
   if (RED == 0) return;
   const int nvals = RED > 0 ? 2 * nv : 1;
-  block_partial_row<R, NVAL>(acc, nvals, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * nvals);
+  block_partial_row<R, NVAL, STPB / 32>(acc, nvals, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * nvals);
   epi_arrive<R>(e, a, s, gridDim.x, nvals);
 }
 
@@ -311,7 +318,7 @@ void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int 
   Epi e = epi ? *epi : Epi{};
   double by = (double)na * op.n * (b ? 3 : 2) * sizeof(cplx<R>) + (double)op.n * sizeof(R);
   if (e.kind == EPI_DOTS) by += (double)na * op.n * nv * sizeof(cplx<R>);
-  ProfScope ps(sizeof(R) == 4 ? PC_STENCIL32 : PC_STENCIL64, by, st);
+  ProfScope ps(prof_stencil_class<R>(op.n), by, st);
   TileGeom G;
   G.K0 = op.K[0];
   G.K1 = op.K[1];

@@ -23,7 +23,7 @@ FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
 CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD = 0, 1, 2, 3
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
-                "misc"]
+                "misc", "stencil_c64_coarse", "krylov_c64_coarse"]
 
 
 class HelmGrid(ctypes.Structure):
