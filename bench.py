@@ -54,7 +54,8 @@ def parse():
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--mode", default="step", choices=["step", "apply"],
+    p.add_argument("--workers", type=int, default=4, help="batch mode: models in flight together")
+    p.add_argument("--mode", default="step", choices=["step", "apply", "batch"],
                    help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
                         "workload's 16 complex64 fields)")
     return p.parse_args()
@@ -86,6 +87,46 @@ def run_apply(args):
         out[name] = dict(gpts=round(st["bytes"] / bpp / t / 1e9, 1), gbs=round(st["bytes"] / t / 1e9, 1),
                          frac=round(st["bytes"] / t / 1e9 / hbm, 3), us_per_launch=round(1e6 * t / st["launches"], 2),
                          peak=hbm, peak_kind=kind)
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(args):
+    """Batching workload: 8 models of uneven size (48^3 ... 160^3, h = 25 m, smooth random
+    velocity) x 32 sources x 3 frequencies (3, 4, 5 Hz) = 768 (source, frequency) pairs per
+    step, evaluated by one helm_misfit_and_gradient_batch call (a work queue of models, each on
+    its own stream).  Reports throughput with `--workers` models in flight and with one."""
+    import torch
+    from paper_1703_09268_gb300 import helm, synth
+    dev = torch.device("cuda", 0)
+    wls = sorted(synth.batch_models(), key=lambda w: -w.n_phys)  # large models first
+    kso, ksi, kco, kci = (int(v) for v in args.smoother.split(","))
+    reqs = []
+    for wl in wls:
+        grid = helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=2)
+        opts = helm.default_opts(precision=helm.MIXED if args.precision == "mixed" else helm.FP64,
+                                 tol=args.tol, tol_inner=args.tol_inner, k_so=kso, k_si=ksi, k_co=kco, k_ci=kci,
+                                 max_batch=args.max_batch or 32)
+        plan = helm.Plan(grid, opts, device=dev)
+        T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        src, Q, rec = T(wl.src_idx, torch.int32), T(wl.Q, torch.complex128), T(wl.rec_idx, torch.int32)
+        # observed data: forward modelling in the true model (input generation, untimed)
+        _, d, _ = helm.helm_forward(plan, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
+                                    want_fields=False)
+        reqs.append(dict(plan=plan, m_phys=T(wl.m0.ravel(), torch.float64), freqs_hz=wl.freqs_hz, src_idx=src, Q=Q,
+                         rec_idx=rec, d_obs=d))
+    units = sum(len(w.freqs_hz) * w.nsrc for w in wls)
+    out = dict(mode="batch", models=[w.name for w in wls], pairs=units, precision=args.precision, tol=args.tol)
+    for nw in (args.workers, 1):
+        for _ in range(max(1, args.warmup)):
+            helm.misfit_and_gradient_batch(reqs, nworkers=nw)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        for _ in range(args.steps):
+            res = helm.misfit_and_gradient_batch(reqs, nworkers=nw)
+        torch.cuda.synchronize()
+        dt = (time.time() - t0) / args.steps
+        out[f"workers_{nw}"] = dict(value=round(units / dt, 3), unit=UNIT, s_per_step=round(dt, 3),
+                                    max_rel_resid=max(r["rel_resid"] for _, _, rep in res for r in rep))
     print(json.dumps(out), flush=True)
 
 
@@ -244,6 +285,8 @@ def main():
         return run_reference(args)
     if args.mode == "apply":
         return run_apply(args)
+    if args.mode == "batch":
+        return run_batch(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -65,7 +65,8 @@ typedef enum {
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
 typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGMRES = 2 } helm_precond;
 typedef enum {
-  HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3
+  HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
+  HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5
 } helm_call;
 
 /* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
@@ -185,6 +186,68 @@ int misfit_and_gradient(helm_plan* plan, const double* m_phys, const double* fre
                         const void* d_obs, const uint8_t* mask, double* f_out, double* g_out,
                         void* workspace, size_t ws_bytes, helm_rhs_report* reports,
                         helm_stream_t stream);
+
+/* Misfit alone (Table derivcosts: one PDE per source and frequency):
+ *   f = sum_{k,s} 1/2 ||P_r u_{k,s} - d_{k,s}||^2,  u = H(m, w_k)^{-1} q_{k,s},
+ * over the (k, s) pairs whose mask byte is non-zero (all when mask is NULL).
+ * Optionally keeps what the gradient needs later (the forward-field store
+ * policy of a differentiable objective):
+ *   R_out  complex128 [nfreq][nsrc][nrec] or NULL: data residuals P_r u - d
+ *          (rows of masked-out pairs are set to zero)
+ *   U_out  complex128 [nfreq][nsrc][n_comp] or NULL: forward fields
+ *          (masked-out pairs are not written)
+ * Other arguments as misfit_and_gradient.  f_out float64 [1]. */
+int helm_misfit(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                const int32_t* rec_idx, int nrec, const void* d_obs, const uint8_t* mask, double* f_out,
+                void* R_out, void* U_out, void* workspace, size_t ws_bytes, helm_rhs_report* reports,
+                helm_stream_t stream);
+
+/* Adjoint-state gradient from stored forward fields (Appendix A; Table
+ * derivstuff, grad f = T* V): for every unmasked (k, s),
+ *   v = -H(m, w_k)^{-H} P_r^T R_{k,s},   g = E^T sum w_k^2 Re(conj(U_{k,s}) v),
+ * with U and R as written by helm_misfit (U complex128 [nfreq][nsrc][n_comp],
+ * R complex128 [nfreq][nsrc][nrec]).  g_out float64 [n_phys] (overwritten).
+ * helm_misfit followed by helm_gradient equals misfit_and_gradient. */
+int helm_gradient(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                  const int32_t* rec_idx, int nrec, const void* R_in, int nsrc, const void* U_in,
+                  const uint8_t* mask, double* g_out, void* workspace, size_t ws_bytes,
+                  helm_rhs_report* reports, helm_stream_t stream);
+
+/* One model's misfit_and_gradient request for helm_misfit_and_gradient_batch
+ * (the paper's distribution over models, sources and frequencies, Sec. 3).
+ * Fields mean what the arguments of misfit_and_gradient mean; `status` is
+ * written with that call's return value. */
+typedef struct {
+  helm_plan* plan;
+  const double* m_phys;
+  const double* freqs_hz;   /* HOST */
+  int nfreq;
+  const int32_t* src_idx;
+  int n_srcloc;
+  const void* Q;
+  int nsrc;
+  const void* wavelet;
+  const int32_t* rec_idx;
+  int nrec;
+  const void* d_obs;
+  const uint8_t* mask;
+  double* f_out;
+  double* g_out;
+  void* workspace;
+  size_t ws_bytes;
+  helm_rhs_report* reports; /* HOST or NULL */
+  helm_stream_t stream;     /* each item on its own stream */
+  int status;               /* out */
+} helm_batch_item;
+
+/* Evaluate every item (models of any size; each with its own plan, data and
+ * workspace).  A work queue hands items to `nworkers` host threads; each
+ * runs misfit_and_gradient on its item's stream, so the kernels of several
+ * models are in flight on the GPU together.  Blocks until all items are done
+ * and returns the worst status (HELM_E_INVAL if items is NULL or nworkers < 1).
+ * Items whose streams or workspaces alias must not be in the same batch. */
+int helm_misfit_and_gradient_batch(helm_batch_item* items, int nitems, int nworkers);
 
 /* helm_apply without a workspace argument (the paper has no counterpart: this
  * is an interface convenience).  For callers that cannot allocate device

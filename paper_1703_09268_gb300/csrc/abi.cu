@@ -243,7 +243,7 @@ int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys)
 
 int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
   if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
-  if (call < HELM_CALL_APPLY || call > HELM_CALL_MISFIT_GRAD) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_GRADIENT) return HELM_E_INVAL;
   *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
   return HELM_OK;
 }
@@ -408,7 +408,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
     if (st == HELM_E_CUDA) return st;
     result = worst(result, st);
     // g += w^2 Re(conj(u) v)
-    launch_grad_accum(c.u, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    launch_grad_accum(c.u, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
     for (int a = 0; a < nb; ++a) {
       SlotReport r = rf[a];
       r.iters += ra[a].iters;
@@ -419,6 +419,102 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
       rf[a] = r;
     }
     fill_reports(reports, g, rf);
+  }
+  launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
+  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  return result;
+}
+
+// (k, s) pairs selected by an optional device mask, in (frequency, source) order.
+static int mask_list(Ctx& c, const uint8_t* mask, int nrhs, std::vector<int>& todo) {
+  todo.clear();
+  if (!mask) {
+    for (int i = 0; i < nrhs; ++i) todo.push_back(i);
+    return HELM_OK;
+  }
+  std::vector<uint8_t> mh(nrhs);
+  cudaMemcpyAsync(mh.data(), mask, nrhs, cudaMemcpyDeviceToHost, c.st);
+  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  for (int i = 0; i < nrhs; ++i)
+    if (mh[i]) todo.push_back(i);
+  return HELM_OK;
+}
+
+int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,
+                int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
+                const void* d_obs, const uint8_t* mask, double* f_out, void* R_out, void* U_out, void* ws,
+                size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out) return HELM_E_INVAL;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_MISFIT, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, src_idx, n_srcloc, rec_idx, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  std::vector<int> todo;
+  if ((st = mask_list(c, mask, nrhs, todo)) != HELM_OK) return st;
+  if (reports)
+    for (int i = 0; i < nrhs; ++i) reports[i] = helm_rhs_report{HELM_OK, 0, 0, 0.0};
+  cudaMemsetAsync(f_out, 0, sizeof(double), c.st);
+  if (R_out) cudaMemsetAsync(R_out, 0, sizeof(double2) * (size_t)nrhs * nrec, c.st);
+  int result = HELM_OK;
+  for (size_t start = 0; start < todo.size(); start += c.B) {
+    const int nb = (int)std::min<size_t>(c.B, todo.size() - start);
+    std::vector<int> g(todo.begin() + start, todo.begin() + start + nb);
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, (const double2*)wavelet, c.slot_f, c.slot_s, nb,
+                   c.q, c.err + 1, c.st);
+    std::vector<SlotReport> rep;
+    st = solve_batch(c, 0, c.q, c.u, nb, rep);
+    if (st == HELM_E_CUDA) return st;
+    result = worst(result, st);
+    for (auto& r : rep) result = worst(result, r.status);
+    launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.slot_f, c.slot_s, nsrc, c.ident, nb,
+                           c.res, c.f_slot, c.st);
+    launch_sum_f(c.f_slot, c.ident, nb, f_out, 1, c.st);
+    if (R_out) launch_copy_fields(c.res, (double2*)R_out, c.ident, nb, c.slot_g, (size_t)nrec, c.st);
+    if (U_out) launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
+    fill_reports(reports, g, rep);
+  }
+  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  return result;
+}
+
+int helm_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* rec_idx,
+                  int nrec, const void* R_in, int nsrc, const void* U_in, const uint8_t* mask, double* g_out,
+                  void* ws, size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!rec_idx || nrec < 1 || !R_in || !U_in || !g_out) return HELM_E_INVAL;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_GRADIENT, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, nullptr, 0, rec_idx, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  std::vector<int> todo;
+  if ((st = mask_list(c, mask, nrhs, todo)) != HELM_OK) return st;
+  if (reports)
+    for (int i = 0; i < nrhs; ++i) reports[i] = helm_rhs_report{HELM_OK, 0, 0, 0.0};
+  cudaMemsetAsync(c.gcomp, 0, sizeof(double) * n, c.st);
+  int result = HELM_OK;
+  for (size_t start = 0; start < todo.size(); start += c.B) {
+    const int nb = (int)std::min<size_t>(c.B, todo.size() - start);
+    std::vector<int> g(todo.begin() + start, todo.begin() + start + nb);
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    // adjoint source -P_r^T R and the adjoint state v = H^{-H}(-P_r^T R)
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_spread(*P, (const double2*)R_in, nrec, rec_idx, nrec, -1.0, c.slot_g, nb, c.q, c.st);
+    std::vector<SlotReport> rep;
+    st = solve_batch(c, 1, c.q, c.v, nb, rep);
+    if (st == HELM_E_CUDA) return st;
+    result = worst(result, st);
+    for (auto& r : rep) result = worst(result, r.status);
+    launch_grad_accum((const double2*)U_in, c.slot_g, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    fill_reports(reports, g, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
   if (sync_check(c) != HELM_OK) return HELM_E_CUDA;

@@ -222,17 +222,19 @@ __global__ void k_spread(GeomArgs g, const double2* __restrict__ r, size_t r_str
   atomicAdd(dst + 1, sign * v.y);
 }
 
-// gcomp[p] += sum_slots w_f^2 Re(conj(u) v), slots summed in order.
-__global__ void k_grad_accum(const double2* __restrict__ u, const double2* __restrict__ v,
-                             const double* __restrict__ w2, const int* __restrict__ slot_f,
-                             const int* __restrict__ slots, int nslots, size_t n,
-                             double* __restrict__ gcomp) {
+// gcomp[p] += sum_slots w_f^2 Re(conj(u) v), slots summed in order.  The
+// field u of slot s is u[u_idx[s]] when u_idx is given (fields stored by the
+// caller in (frequency, source) order), else u[s].
+__global__ void k_grad_accum(const double2* __restrict__ u, const int* __restrict__ u_idx,
+                             const double2* __restrict__ v, const double* __restrict__ w2,
+                             const int* __restrict__ slot_f, const int* __restrict__ slots, int nslots,
+                             size_t n, double* __restrict__ gcomp) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double acc = gcomp[p];
   for (int a = 0; a < nslots; ++a) {
     const int s = slots[a];
-    const double2 uu = u[(size_t)s * n + p];
+    const double2 uu = u[(size_t)(u_idx ? u_idx[s] : s) * n + p];
     const double2 vv = v[(size_t)s * n + p];
     acc += w2[slot_f[s]] * (uu.x * vv.x + uu.y * vv.y);
   }
@@ -364,10 +366,10 @@ void launch_spread(const helm_plan& P, const double2* r, size_t r_stride, const 
   count_launch();
 }
 
-void launch_grad_accum(const double2* u, const double2* v, const double* w2, const int* slot_f,
+void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
                        const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st) {
   if (nslots <= 0) return;
-  k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, v, w2, slot_f, slots, nslots, n, gcomp);
+  k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n, gcomp);
   count_launch();
 }
 

@@ -128,7 +128,8 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   const size_t n0 = P.lev[0].n;
   C.q = bp.take<double2>((size_t)B * n0);
   C.u = bp.take<double2>((size_t)B * n0);
-  if (call != HELM_CALL_FORWARD) C.v = bp.take<double2>((size_t)B * n0);
+  if (call == HELM_CALL_ADJOINT || call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT)
+    C.v = bp.take<double2>((size_t)B * n0);
   C.nrm = bp.take<double>(B);
   C.qn = bp.take<double>(B);
   if (C.mixed) {
@@ -139,11 +140,11 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   } else {
     layout_hierarchy<double>(bp, P, C.h64, B);
   }
-  if (call == HELM_CALL_MISFIT_GRAD) {
+  if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_MISFIT) {
     C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
     C.f_slot = bp.take<double>(B);
-    C.gcomp = bp.take<double>(n0);
   }
+  if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT) C.gcomp = bp.take<double>(n0);
   return bp.off;
 }
 
@@ -473,6 +474,7 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
   if (!c.mixed) {
     st = outer_solve<double>(c, q, u, o.tol, &ko, true);
     cudaMemcpyAsync(rn.data(), c.h64.inst[0].ks.rnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
+    cudaMemcpyAsync(qn.data(), c.qn, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
     for (int a = 0; a < nb; ++a) rep[a].refine = 1;
   } else {
     // FP64 iterative refinement around complex64 inner solves:

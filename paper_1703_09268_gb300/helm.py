@@ -21,7 +21,7 @@ HELM_OK, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_CUDA, HELM_E_NOCONV, HELM_E_NONFINIT
     0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
-CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD = 0, 1, 2, 3
+CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT = 0, 1, 2, 3, 4, 5
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
                 "misc", "stencil_c64_coarse", "krylov_c64_coarse"]
 
@@ -46,8 +46,19 @@ class HelmRhsReport(ctypes.Structure):
                 ("rel_resid", ctypes.c_double)]
 
 
-EXPORTS = ["helm_default_opts", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
+class HelmBatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("m_phys", ctypes.c_void_p), ("freqs_hz", ctypes.POINTER(ctypes.c_double)),
+                ("nfreq", ctypes.c_int), ("src_idx", ctypes.c_void_p), ("n_srcloc", ctypes.c_int),
+                ("Q", ctypes.c_void_p), ("nsrc", ctypes.c_int), ("wavelet", ctypes.c_void_p),
+                ("rec_idx", ctypes.c_void_p), ("nrec", ctypes.c_int), ("d_obs", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("f_out", ctypes.c_void_p), ("g_out", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t),
+                ("reports", ctypes.POINTER(HelmRhsReport)), ("stream", ctypes.c_void_p), ("status", ctypes.c_int)]
+
+
+EXPORTS = ["helm_default_opts", "helm_misfit_and_gradient_batch", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
            "helm_workspace_size", "helm_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
+           "helm_misfit", "helm_gradient",
            "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read"]
 
 
@@ -70,6 +81,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(HelmRhsReport), P]
     lib.misfit_and_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, S,
                                         ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_misfit.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, P, S,
+                                ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, P, P, S,
+                                  ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_misfit_and_gradient_batch.argtypes = [ctypes.POINTER(HelmBatchItem), I, I]
     lib.helm_status_string.argtypes = [I]
     lib.helm_status_string.restype = ctypes.c_char_p
     lib.helm_kernel_launch_count.argtypes = []
@@ -316,6 +332,112 @@ def misfit_and_gradient(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs
                                      _ptr(d_obs), _ptr(mask), _ptr(f), _ptr(g), ws, nb, rep, _stream(dev))
     _check(code, "misfit_and_gradient", allow_noconv=True)
     return f, g, reports_to_list(rep)
+
+
+def helm_misfit(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, mask=None,
+                keep_residuals=False, keep_fields=False, f_out=None):
+    """f only (one solve per pair); optionally the data residuals R [nfreq, nsrc, nrec]
+    and forward fields U [nfreq, nsrc, n_comp] the gradient needs.
+    Returns (f, R or None, U or None, reports)."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(src_idx, torch.int32, "src_idx")
+    _dev(Q, torch.complex128, "Q")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    _dev(d_obs, torch.complex128, "d_obs")
+    if wavelet is not None:
+        _dev(wavelet, torch.complex128, "wavelet")
+    if mask is not None:
+        _dev(mask, torch.uint8, "mask")
+    nfreq = len(np.atleast_1d(freqs_hz))
+    _check_common(plan, m_phys, src_idx, Q, wavelet, nfreq)
+    nsrc = Q.shape[1]
+    nrec = rec_idx.numel()
+    _need(tuple(d_obs.shape) == (nfreq, nsrc, nrec), "d_obs must be [nfreq, nsrc, nrec]")
+    if mask is not None:
+        _need(mask.numel() == nfreq * nsrc, "mask must be [nfreq, nsrc]")
+    dev = m_phys.device
+    f = torch.empty(1, dtype=torch.float64, device=dev) if f_out is None else f_out
+    R = torch.empty((nfreq, nsrc, nrec), dtype=torch.complex128, device=dev) if keep_residuals else None
+    U = torch.zeros((nfreq, nsrc, plan.n_comp), dtype=torch.complex128, device=dev) if keep_fields else None
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_MISFIT, nfreq, nsrc, nrec))
+    code = lib().helm_misfit(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx), src_idx.numel(),
+                             _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(d_obs), _ptr(mask), _ptr(f),
+                             _ptr(R), _ptr(U), ws, nb, rep, _stream(dev))
+    _check(code, "helm_misfit", allow_noconv=True)
+    return f, R, U, reports_to_list(rep)
+
+
+def helm_gradient(plan: Plan, m_phys, freqs_hz, rec_idx, R, U, mask=None, g_out=None):
+    """Adjoint-state gradient from stored residuals R and fields U (helm_misfit)."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    _dev(R, torch.complex128, "R")
+    _dev(U, torch.complex128, "U")
+    _check_common(plan, m_phys)
+    nfreq, nsrc, nrec = R.shape
+    _need(nfreq == len(np.atleast_1d(freqs_hz)) and nrec == rec_idx.numel(), "R must be [nfreq, nsrc, nrec]")
+    _need(tuple(U.shape) == (nfreq, nsrc, plan.n_comp), "U must be [nfreq, nsrc, n_comp]")
+    if mask is not None:
+        _dev(mask, torch.uint8, "mask")
+        _need(mask.numel() == nfreq * nsrc, "mask must be [nfreq, nsrc]")
+    dev = m_phys.device
+    g = torch.empty(plan.n_phys, dtype=torch.float64, device=dev) if g_out is None else g_out
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_GRADIENT, nfreq, nsrc, nrec))
+    code = lib().helm_gradient(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(rec_idx), nrec, _ptr(R), nsrc,
+                               _ptr(U), _ptr(mask), _ptr(g), ws, nb, rep, _stream(dev))
+    _check(code, "helm_gradient", allow_noconv=True)
+    return g, reports_to_list(rep)
+
+
+def misfit_and_gradient_batch(requests, nworkers: int = 4):
+    """misfit_and_gradient for several models at once (helm_misfit_and_gradient_batch).
+
+    `requests` is a list of dicts with keys plan, m_phys, freqs_hz, src_idx, Q,
+    rec_idx, d_obs and optionally wavelet, mask.  Every request gets its own CUDA
+    stream and workspace.  Returns a list of (f, g, reports)."""
+    n = len(requests)
+    _need(len({id(r["plan"]) for r in requests}) == n, "every request needs its own Plan (workspaces must not alias)")
+    items = (HelmBatchItem * n)()
+    keep, outs = [], []
+    for i, r in enumerate(requests):
+        plan = r["plan"]
+        m, src, Q, rec, d = r["m_phys"], r["src_idx"], r["Q"], r["rec_idx"], r["d_obs"]
+        wav, mask = r.get("wavelet"), r.get("mask")
+        _dev(m, torch.float64, "m_phys")
+        _dev(src, torch.int32, "src_idx")
+        _dev(Q, torch.complex128, "Q")
+        _dev(rec, torch.int32, "rec_idx")
+        _dev(d, torch.complex128, "d_obs")
+        nfreq = len(np.atleast_1d(r["freqs_hz"]))
+        _check_common(plan, m, src, Q, wav, nfreq)
+        nsrc, nrec = Q.shape[1], rec.numel()
+        _need(tuple(d.shape) == (nfreq, nsrc, nrec), "d_obs must be [nfreq, nsrc, nrec]")
+        f = torch.empty(1, dtype=torch.float64, device=m.device)
+        g = torch.empty(plan.n_phys, dtype=torch.float64, device=m.device)
+        rep = _reports(nfreq * nsrc)
+        ws, nb = plan.workspace(plan.workspace_size(CALL_MISFIT_GRAD, nfreq, nsrc, nrec))
+        stream = torch.cuda.Stream(device=m.device)
+        fr = _freqs(r["freqs_hz"])
+        it = items[i]
+        it.plan = plan._h
+        it.m_phys, it.freqs_hz, it.nfreq = m.data_ptr(), fr, nfreq
+        it.src_idx, it.n_srcloc, it.Q, it.nsrc = src.data_ptr(), src.numel(), Q.data_ptr(), nsrc
+        it.wavelet = wav.data_ptr() if wav is not None else None
+        it.rec_idx, it.nrec, it.d_obs = rec.data_ptr(), nrec, d.data_ptr()
+        it.mask = mask.data_ptr() if mask is not None else None
+        it.f_out, it.g_out = f.data_ptr(), g.data_ptr()
+        it.workspace, it.ws_bytes = ws.value, nb
+        it.reports = rep
+        it.stream = stream.cuda_stream
+        keep.append((fr, stream))
+        outs.append((f, g, rep))
+    # the inputs were written on the caller's stream: make them visible to every item's stream
+    torch.cuda.current_stream().synchronize()
+    code = lib().helm_misfit_and_gradient_batch(items, n, int(nworkers))
+    _check(code, "helm_misfit_and_gradient_batch", allow_noconv=True)
+    return [(f, g, reports_to_list(rep)) for f, g, rep in outs]
 
 
 def kernel_launch_count() -> int:

@@ -1,0 +1,135 @@
+"""The differentiable FWI objective (torch.autograd.Function over the C ABI).
+
+* every forward-field policy (eager, store, recompute, auto) returns the
+  oracle's f and adjoint-state gradient;
+* the gradient matches central differences of the objective itself;
+* the incoming gradient scales the result (chain rule through torch);
+* on a 32^3 crop of the differentiation workload the gradient matches the
+  oracle's (stored fixture written by tests/golden/make_crop32.py).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import helmholtz as O
+from paper_1703_09268_gb300 import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::scipy.sparse.SparseEfficiencyWarning")]
+
+DEV = torch.device("cuda:0")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1703_09268_gb300 import autograd, helm
+    return helm, autograd
+
+
+def T(a, dt):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+
+
+def rel(a, b):
+    a, b = np.asarray(a).ravel(), np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def small():
+    rng = np.random.default_rng(31)
+    n, h = (15, 13, 14), 50.0
+    g = O.make_grid(3, n, h, (6, 6, 6), 4500.0, levels=2)
+    v = synth.layered_velocity(rng, n, nlayers=4, smooth=1.5)
+    mt = synth.slowness2(v)
+    m0 = synth.slowness2(synth._gaussian_smooth(v, 4.0))
+    src, Q = synth.point_sources(n, [(3, 3, 2), (11, 9, 2), (7, 6, 2)])
+    rec = synth.surface_receivers(n, 0)
+    freqs = np.array([2.5, 4.0])
+    _, d = O.forward(g, mt, freqs, src, Q, rec)
+    f, gr = O.misfit_and_gradient(g, m0, freqs, src, Q, rec, d)
+    return dict(n=n, h=h, m0=m0, src=src, Q=Q, rec=rec, freqs=freqs, d=d, f=f, g=gr)
+
+
+def problem(helm, autograd, s, policy, tol=1e-11):
+    plan = helm.Plan(helm.make_grid(3, s["n"], s["h"], (6, 6, 6), 4500.0, levels=2), helm.default_opts(tol=tol),
+                     device=DEV)
+    return autograd.FWIProblem(plan=plan, freqs_hz=s["freqs"], src_idx=T(s["src"], torch.int32),
+                               Q=T(s["Q"], torch.complex128), rec_idx=T(s["rec"], torch.int32),
+                               d_obs=T(s["d"], torch.complex128), policy=policy)
+
+
+@pytest.mark.parametrize("policy", ["eager", "store", "recompute", "auto"])
+def test_policies_match_oracle(mods, small, policy):
+    helm, autograd = mods
+    p = problem(helm, autograd, small, policy)
+    m = T(small["m0"].ravel(), torch.float64).requires_grad_(True)
+    f = autograd.fwi_objective(m, p)
+    (g,) = torch.autograd.grad(f, m)
+    assert abs(f.item() - small["f"]) <= 1e-8 * abs(small["f"])
+    assert rel(g.cpu().numpy(), small["g"]) <= 1e-8
+
+
+def test_directional_derivative_matches_central_differences(mods, small):
+    helm, autograd = mods
+    p = problem(helm, autograd, small, "store", tol=1e-12)
+    m0 = small["m0"].ravel()
+    m = T(m0, torch.float64).requires_grad_(True)
+    (g,) = torch.autograd.grad(autograd.fwi_objective(m, p), m)
+    g = g.cpu().numpy()
+    rng = np.random.default_rng(5)
+
+    def fval(mm):
+        with torch.no_grad():
+            return autograd.fwi_objective(T(mm, torch.float64), p).item()
+
+    for _ in range(3):
+        dm = rng.standard_normal(m0.size) * m0
+        t = 2e-3
+
+        def cd(s):
+            return (fval(m0 + s * dm) - fval(m0 - s * dm)) / (2 * s)
+
+        fd = (4 * cd(t / 2) - cd(t)) / 3
+        an = float(g @ dm)
+        assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+
+
+def test_incoming_gradient_scales(mods, small):
+    helm, autograd = mods
+    p = problem(helm, autograd, small, "eager")
+    m = T(small["m0"].ravel(), torch.float64).requires_grad_(True)
+    loss = 3.0 * autograd.fwi_objective(m, p) + (m * m).sum()
+    (g,) = torch.autograd.grad(loss, m)
+    expect = 3.0 * small["g"].ravel() + 2.0 * small["m0"].ravel()
+    assert rel(g.cpu().numpy(), expect) <= 1e-8
+
+
+def test_crop32_gradient_matches_oracle_fixture(mods):
+    helm, autograd = mods
+    with open(os.path.join(GOLDEN, "crop32_gradient.json")) as fh:
+        gold = json.load(fh)
+    d_obs = np.load(os.path.join(GOLDEN, "crop32_dobs.npz"))["d_obs"]
+    s = gold["spec"]
+    wl = synth.workload_3d_multifreq(seed=s["seed"], n=s["n"], h=s["h"], npml=s["npml"], nsx=s["nsx"], nsy=s["nsy"],
+                                     nfreq=s["nfreq"], fmin=s["fmin"], fmax=s["fmax"])
+    plan = helm.Plan(helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=s["levels"]),
+                     helm.default_opts(tol=1e-11), device=DEV)
+    p = autograd.FWIProblem(plan=plan, freqs_hz=wl.freqs_hz, src_idx=T(wl.src_idx, torch.int32),
+                            Q=T(wl.Q, torch.complex128), rec_idx=T(wl.rec_idx, torch.int32),
+                            d_obs=T(d_obs, torch.complex128), policy="auto")
+    m = T(wl.m0.ravel(), torch.float64).requires_grad_(True)
+    f = autograd.fwi_objective(m, p)
+    (g,) = torch.autograd.grad(f, m)
+    g = g.cpu().numpy()
+    assert abs(f.item() - gold["f"]) <= 1e-8 * abs(gold["f"])
+    assert abs(np.linalg.norm(g) - gold["g_norm"]) <= 1e-8 * gold["g_norm"]
+    idx = np.asarray(gold["sample_idx"])
+    assert rel(g[idx], gold["g_samples"]) <= 1e-8
+    proj = np.random.default_rng(123).standard_normal((8, g.size)) @ g
+    assert rel(proj, gold["projections"]) <= 1e-8

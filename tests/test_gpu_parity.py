@@ -4,7 +4,7 @@ same seeded inputs.
 Tolerances (relative L2):
   * operator apply, FP64: 1e-13 (same formula, different rounding order);
   * operator apply, complex64: 2e-6 (single-precision coefficients and sums);
-  * FP64 solves to residual 1e-13 vs the oracle's direct solve: 1e-10;
+  * FP64 solves to residual 5e-14 vs the oracle's direct solve: 1e-10;
   * complex64 inner solves under FP64 refinement to residual 1e-11: 1e-8.
 These are the tolerances of the method's statement (1e-10 FP64, 1e-8 mixed).
 """
@@ -105,12 +105,13 @@ def wl2d():
 
 
 OPTS = {
-    "fp64-mlgmres": dict(precision=0, precond=2, tol=1e-14),
-    "fp64-none": dict(precision=0, precond=0, k_inner=30, tol=1e-14, max_cycles=2000),
-    "fp64-jacobi": dict(precision=0, precond=1, k_inner=20, tol=1e-14, max_cycles=2000, jacobi_sweeps=2),
+    # FP64 solves stop at 5e-14: the residual floor of the 2D problem is ~3e-14
+    "fp64-mlgmres": dict(precision=0, precond=2, tol=5e-14),
+    "fp64-none": dict(precision=0, precond=0, k_inner=30, tol=5e-14, max_cycles=2000),
+    "fp64-jacobi": dict(precision=0, precond=1, k_inner=20, tol=5e-14, max_cycles=2000, jacobi_sweeps=2),
     "mixed-mlgmres": dict(precision=1, precond=2, tol=1e-11),
     "mixed-mlgmres-arnoldi-smoother": dict(precision=1, precond=2, tol=1e-11, sstep=0, reorth=0),
-    "fp64-mlgmres-arnoldi-smoother": dict(precision=0, precond=2, tol=1e-14, sstep=0),
+    "fp64-mlgmres-arnoldi-smoother": dict(precision=0, precond=2, tol=5e-14, sstep=0),
     "mixed-none": dict(precision=1, precond=0, k_inner=30, tol=1e-11, max_cycles=400),
 }
 
