@@ -381,7 +381,9 @@ def main():
                     frac=round(achieved / hbm, 3), traffic=None, peak_kind=hbm_kind,
                     launches=dn["launches"], avg_launch_us=round(1e3 * dn["ms"] / max(dn["launches"], 1), 2),
                     bytes_per_launch=dn["bytes"] / max(dn["launches"], 1),
-                    share={k: round(v["ms"] / tot_ms, 3) for k, v in prof.items() if v["launches"]})
+                    share={k: round(v["ms"] / tot_ms, 3) for k, v in prof.items() if v["launches"]},
+                    class_frac={k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm, 3)
+                                for k, v in prof.items() if v["launches"] and v["bytes"] > 0 and v["ms"] > 0})
     st = prof["stencil_c64"] if prof["stencil_c64"]["launches"] else prof["stencil_c128"]
     sbytes_pt = 16.0 if prof["stencil_c64"]["launches"] else 32.0
     stencil = dict(gpts=round(st["bytes"] / sbytes_pt / (st["ms"] / 1e3) / 1e9, 1),

@@ -293,7 +293,9 @@ typedef enum {
   HELM_PROF_MISC = 7,         /* conversions, zero fills, Jacobi */
   HELM_PROF_STENCIL_C64_COARSE = 8, /* complex64 stencil launches on grids below 200000 nodes */
   HELM_PROF_KRYLOV_C64_COARSE = 9,  /* complex64 vector passes on grids below 200000 nodes */
-  HELM_PROF_NCLASS = 10
+  HELM_PROF_GRAM_C64 = 10,    /* s-step Gram passes, complex64, fine grids */
+  HELM_PROF_UPDATE_C64 = 11,  /* solution updates (and recursive residuals), complex64, fine grids */
+  HELM_PROF_NCLASS = 12
 } helm_prof_class;
 int helm_profile_enable(int on);
 int helm_profile_read(int cls, uint64_t* launches, double* ms, double* bytes);

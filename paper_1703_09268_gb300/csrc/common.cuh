@@ -63,15 +63,15 @@ inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_o
 // algorithmic bytes are accumulated.
 enum ProfClass {
   PC_STENCIL32 = 0, PC_STENCIL64, PC_GS32, PC_GS64, PC_SMALL, PC_TRANSFER, PC_FWI, PC_MISC,
-  PC_STENCIL32_COARSE, PC_GS32_COARSE, PC_COUNT
+  PC_STENCIL32_COARSE, PC_GS32_COARSE, PC_GRAM32, PC_UPDATE32, PC_COUNT
 };
 // Launches on grids below this many nodes per field are booked to the coarse classes.
 constexpr size_t PROF_COARSE_N = 200000;
 template <typename R> inline int prof_stencil_class(size_t n) {
   return sizeof(R) == 8 ? PC_STENCIL64 : (n < PROF_COARSE_N ? PC_STENCIL32_COARSE : PC_STENCIL32);
 }
-template <typename R> inline int prof_gs_class(size_t n) {
-  return sizeof(R) == 8 ? PC_GS64 : (n < PROF_COARSE_N ? PC_GS32_COARSE : PC_GS32);
+template <typename R> inline int prof_gs_class(size_t n, int fine_class = PC_GS32) {
+  return sizeof(R) == 8 ? PC_GS64 : (n < PROF_COARSE_N ? PC_GS32_COARSE : fine_class);
 }
 struct ProfScope {
   ProfScope(int cls, double bytes, cudaStream_t st);
@@ -175,6 +175,11 @@ void launch_gs(int mode, const cplx<R>* V, size_t vstride, int nv, const cplx<R>
                const cplx<R>* w, Scale<R> ws, cplx<R>* out, const int* act, int na, size_t n,
                const Epi& e, cudaStream_t st);
 int reduction_blocks(int na, size_t n, int threads);
+// End of an s-step cycle: x += sum_{i<s} c_i W_i (x = ... when xzero) and, with
+// recur, W_0 <- W_0 - sum_{i<s} c_i W_{i+1} in the same pass.
+template <typename R>
+void launch_sstep_update(cplx<R>* V, size_t vstride, int s, const cplx<R>* coef, cplx<R>* x, const int* act, int na,
+                         size_t n, int recur, int xzero, cudaStream_t st);
 // Gram pass of an s-step cycle over W_0..W_s (EPI_GRAM epilogue).
 template <typename R>
 void launch_gram(const cplx<R>* V, size_t vstride, int s, const int* act, int na, size_t n, const Epi& e,

@@ -7,6 +7,7 @@
 // consumer, so no normalisation pass is needed.  Each pass carries its own
 // deterministic reduction and per-slot epilogue (reduce.cuh).
 #include <cmath>
+#include <cstdint>
 
 #include "reduce.cuh"
 
@@ -98,49 +99,190 @@ void gs_pick(int nv, dim3 grd, cudaStream_t st, const cplx<R>* V, size_t vstride
     gs_go<R, MODE, KMAX + 1>(grd, st, V, vstride, nv, coef, w, ws, out, act, n, chunk, e);
 }
 
-// Gram pass of an s-step cycle: raw <W_i, W_j> (1 <= i <= j <= S) and
-// <W_i, W_0> over the stored basis W_0..W_S, folded into EPI_GRAM.
+// Elements p and p+1 of a complex field whose global index p is even: one
+// 16-byte access in single precision, two in double.
+template <typename R> __device__ __forceinline__ void ld_pair(const cplx<R>* q, cplx<R>& a, cplx<R>& b) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(q);
+    a = make_float2(t.x, t.y);
+    b = make_float2(t.z, t.w);
+  } else {
+    a = q[0];
+    b = q[1];
+  }
+}
+template <typename R> __device__ __forceinline__ void st_pair(cplx<R>* q, cplx<R> a, cplx<R> b) {
+  if constexpr (sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(q) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    q[0] = a;
+    q[1] = b;
+  }
+}
+
+// Paired traversal of one slot's field: with VEC the points are visited in
+// pairs (p, p+1) starting at the first even global index, and the odd head /
+// tail points (at most one each) are returned separately.
+struct PairSplit {
+  int head;        // 1 when the slot's first point has an odd global index
+  size_t npair;    // pairs after the head
+  bool tail;       // one point left after the pairs
+};
+__device__ __forceinline__ PairSplit pair_split(size_t slot_base, size_t n) {
+  PairSplit ps;
+  ps.head = (int)(slot_base & 1) && n > 0 ? 1 : 0;
+  ps.npair = (n - ps.head) >> 1;
+  ps.tail = ((n - ps.head) & 1) != 0;
+  return ps;
+}
+
+// Gram sums of one point: <W_i, W_j> (1 <= i <= j <= S), <W_i, W_0>, ||W_0||^2.
 template <typename R, int S>
-__global__ void __launch_bounds__(GS_THREADS, sizeof(R) == 4 ? 3 : 2)
+__device__ __forceinline__ void gram_point(const cplx<R>* w, R* acc) {
+  int k = 0;
+#pragma unroll
+  for (int i = 1; i <= S; ++i) {
+#pragma unroll
+    for (int j = i; j <= S; ++j, ++k) {
+      acc[2 * k] = fma(w[i].x, w[j].x, fma(w[i].y, w[j].y, acc[2 * k]));
+      acc[2 * k + 1] = fma(w[i].x, w[j].y, fma(-w[i].y, w[j].x, acc[2 * k + 1]));
+    }
+  }
+#pragma unroll
+  for (int i = 1; i <= S; ++i, ++k) {
+    acc[2 * k] = fma(w[i].x, w[0].x, fma(w[i].y, w[0].y, acc[2 * k]));
+    acc[2 * k + 1] = fma(w[i].x, w[0].y, fma(-w[i].y, w[0].x, acc[2 * k + 1]));
+  }
+  acc[2 * k] = fma(w[0].x, w[0].x, fma(w[0].y, w[0].y, acc[2 * k]));
+}
+
+// Gram pass of an s-step cycle: raw <W_i, W_j> (1 <= i <= j <= S) and
+// <W_i, W_0> over the stored basis W_0..W_S, folded into EPI_GRAM.  Block b of
+// a slot covers units [b*chunk, (b+1)*chunk), a unit being a point (VEC false)
+// or a pair of points (VEC true).
+template <typename R, int S, bool VEC>
+__global__ void __launch_bounds__(GS_THREADS, VEC ? 2 : (sizeof(R) == 4 ? 3 : 2))
 k_gram(const cplx<R>* __restrict__ V, size_t vstride, const int* __restrict__ act, size_t n, size_t chunk, Epi e) {
   using C = cplx<R>;
   constexpr int NV = gram_nvals(S);
   const int a = blockIdx.y;
   const int s = act[a];
-  const size_t beg = (size_t)blockIdx.x * chunk;
-  const size_t end = min(n, beg + chunk);
   const C* Vs = V + (size_t)s * n;
   R acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = R(0);
-  for (size_t p = beg + threadIdx.x; p < end; p += GS_THREADS) {
-    C w[S + 1];
+  if (VEC) {
+    const PairSplit sp = pair_split((size_t)s * n, n);
+    const size_t beg = (size_t)blockIdx.x * chunk;
+    const size_t end = min(sp.npair, beg + chunk);
+    for (size_t q = beg + threadIdx.x; q < end; q += GS_THREADS) {
+      const size_t p = sp.head + 2 * q;
+      C wa[S + 1], wb[S + 1];
 #pragma unroll
-    for (int i = 0; i <= S; ++i) w[i] = Vs[i * vstride + p];
-    int k = 0;
+      for (int i = 0; i <= S; ++i) ld_pair<R>(Vs + i * vstride + p, wa[i], wb[i]);
+      gram_point<R, S>(wa, acc);
+      gram_point<R, S>(wb, acc);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C w[S + 1];
+      if (sp.head) {
 #pragma unroll
-    for (int i = 1; i <= S; ++i) {
+        for (int i = 0; i <= S; ++i) w[i] = Vs[i * vstride];
+        gram_point<R, S>(w, acc);
+      }
+      if (sp.tail) {
 #pragma unroll
-      for (int j = i; j <= S; ++j, ++k) {
-        acc[2 * k] = fma(w[i].x, w[j].x, fma(w[i].y, w[j].y, acc[2 * k]));
-        acc[2 * k + 1] = fma(w[i].x, w[j].y, fma(-w[i].y, w[j].x, acc[2 * k + 1]));
+        for (int i = 0; i <= S; ++i) w[i] = Vs[i * vstride + n - 1];
+        gram_point<R, S>(w, acc);
       }
     }
+  } else {
+    const size_t beg = (size_t)blockIdx.x * chunk;
+    const size_t end = min(n, beg + chunk);
+    for (size_t p = beg + threadIdx.x; p < end; p += GS_THREADS) {
+      C w[S + 1];
 #pragma unroll
-    for (int i = 1; i <= S; ++i, ++k) {
-      acc[2 * k] = fma(w[i].x, w[0].x, fma(w[i].y, w[0].y, acc[2 * k]));
-      acc[2 * k + 1] = fma(w[i].x, w[0].y, fma(-w[i].y, w[0].x, acc[2 * k + 1]));
+      for (int i = 0; i <= S; ++i) w[i] = Vs[i * vstride + p];
+      gram_point<R, S>(w, acc);
     }
-    acc[2 * k] = fma(w[0].x, w[0].x, fma(w[0].y, w[0].y, acc[2 * k]));
   }
   block_partial_row<R, NV, GS_THREADS / 32>(acc, NV, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * NV);
   epi_arrive<R>(e, a, s, gridDim.x, NV);
 }
 
+// End of an s-step cycle: x += sum_{i<S} y_i W_i (x = sum_i y_i W_i when
+// xzero), and with recur the next residual by recurrence in the same pass,
+// W_0 <- W_0 - sum_{i<S} y_i W_{i+1} (= b - H x_new since W_{i+1} = H W_i).
 template <typename R, int S>
+__device__ __forceinline__ void sstep_point(const cplx<R>* cf, const cplx<R>* w, cplx<R>& xv, cplx<R>& r,
+                                            bool recur) {
+  r = w[0];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    xv = cfma(cf[i], w[i], xv);
+    if (recur) r = cfms(cf[i], w[i + 1], r);
+  }
+}
+
+template <typename R, int S, bool VEC>
+__global__ void __launch_bounds__(GS_THREADS)
+k_sstep_update(cplx<R>* V, size_t vstride, const cplx<R>* __restrict__ coef, cplx<R>* x,
+               const int* __restrict__ act, size_t n, int recur, int xzero) {
+  using C = cplx<R>;
+  const int s = act[blockIdx.y];
+  C cf[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) cf[i] = coef[(size_t)s * (KMAX + 1) + i];
+  C* Vs = V + (size_t)s * n;
+  C* X = x + (size_t)s * n;
+  const int nw = recur ? S + 1 : S;  // W_S only feeds the recurrence
+  const C zero = mkc(R(0), R(0));
+  auto one = [&](size_t p) {
+    C w[S + 1];
+#pragma unroll
+    for (int i = 0; i <= S; ++i) w[i] = i < nw ? Vs[i * vstride + p] : zero;
+    C xv = xzero ? zero : X[p], r;
+    sstep_point<R, S>(cf, w, xv, r, recur);
+    X[p] = xv;
+    if (recur) Vs[p] = r;
+  };
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if (VEC) {
+    const PairSplit sp = pair_split((size_t)s * n, n);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < sp.npair; q += stride) {
+      const size_t p = sp.head + 2 * q;
+      C wa[S + 1], wb[S + 1];
+#pragma unroll
+      for (int i = 0; i <= S; ++i) {
+        if (i < nw) ld_pair<R>(Vs + i * vstride + p, wa[i], wb[i]);
+        else wa[i] = wb[i] = zero;
+      }
+      C xa = zero, xb = zero, ra, rb;
+      if (!xzero) ld_pair<R>(X + p, xa, xb);
+      sstep_point<R, S>(cf, wa, xa, ra, recur);
+      sstep_point<R, S>(cf, wb, xb, rb, recur);
+      st_pair<R>(X + p, xa, xb);
+      if (recur) st_pair<R>(Vs + p, ra, rb);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (sp.head) one(0);
+      if (sp.tail) one(n - 1);
+    }
+  } else {
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) one(p);
+  }
+}
+
+template <typename R, int S, bool VEC>
+void sup_go(dim3 grd, cudaStream_t st, cplx<R>* V, size_t vstride, const cplx<R>* coef, cplx<R>* x, const int* act,
+            size_t n, int recur, int xzero) {
+  k_sstep_update<R, S, VEC><<<grd, GS_THREADS, 0, st>>>(V, vstride, coef, x, act, n, recur, xzero);
+}
+
+template <typename R, int S, bool VEC>
 void gram_go(dim3 grd, cudaStream_t st, const cplx<R>* V, size_t vstride, const int* act, size_t n, size_t chunk,
              const Epi& e) {
-  k_gram<R, S><<<grd, GS_THREADS, 0, st>>>(V, vstride, act, n, chunk, e);
+  k_gram<R, S, VEC><<<grd, GS_THREADS, 0, st>>>(V, vstride, act, n, chunk, e);
 }
 
 __global__ void k_to32_scaled(const double2* __restrict__ r, const double* __restrict__ rnorm,
@@ -196,7 +338,8 @@ void launch_gs(int mode, const cplx<R>* V, size_t vstride, int nv, const cplx<R>
   double vecs = nv + 1;                             // V_0..V_{nv-1} and w read once
   if (mode == GS_SUB_STORE_NORM && out) vecs += 1;  // plus the stored result
   if (mode == GS_ADD_STORE) vecs += 1;              // x read and written
-  ProfScope ps(prof_gs_class<R>(n), vecs * na * n * sizeof(cplx<R>), st);
+  ProfScope ps(prof_gs_class<R>(n, mode == GS_ADD_STORE ? PC_UPDATE32 : PC_GS32), vecs * na * n * sizeof(cplx<R>),
+               st);
   switch (mode) {
     case GS_DOT: gs_pick<R, GS_DOT>(nv, grd, st, V, vstride, coef, w, ws, out, act, n, chunk, e); break;
     case GS_SUB_DOT: gs_pick<R, GS_SUB_DOT>(nv, grd, st, V, vstride, coef, w, ws, out, act, n, chunk, e); break;
@@ -208,24 +351,64 @@ void launch_gs(int mode, const cplx<R>* V, size_t vstride, int nv, const cplx<R>
   count_launch();
 }
 
+// Paired 16-byte accesses need every basis vector of a slot to start at the
+// same parity (even vstride) and 16-byte aligned bases; single precision only.
+template <typename R>
+static bool use_pairs(const void* V, size_t vstride, const void* x) {
+  return sizeof(R) == 4 && vstride % 2 == 0 && ((uintptr_t)V & 15) == 0 && ((uintptr_t)x & 15) == 0;
+}
+
+template <typename R, template <typename, int, bool> class F, typename... A>
+static void s_dispatch(int s, bool vec, A&&... args) {
+  switch (s * 2 + (vec ? 1 : 0)) {
+#define HELM_S_CASE(S)                                       \
+  case 2 * S: F<R, S, false>::go(args...); break;            \
+  case 2 * S + 1: F<R, S, true>::go(args...); break;
+    HELM_S_CASE(1) HELM_S_CASE(2) HELM_S_CASE(3) HELM_S_CASE(4)
+    HELM_S_CASE(5) HELM_S_CASE(6) HELM_S_CASE(7) HELM_S_CASE(8)
+#undef HELM_S_CASE
+    default: break;
+  }
+}
+template <typename R, int S, bool VEC> struct GramGo {
+  static void go(dim3 grd, cudaStream_t st, const cplx<R>* V, size_t vstride, const int* act, size_t n, size_t chunk,
+                 const Epi& e) {
+    gram_go<R, S, VEC && sizeof(R) == 4>(grd, st, V, vstride, act, n, chunk, e);
+  }
+};
+template <typename R, int S, bool VEC> struct SupGo {
+  static void go(dim3 grd, cudaStream_t st, cplx<R>* V, size_t vstride, const cplx<R>* coef, cplx<R>* x,
+                 const int* act, size_t n, int recur, int xzero) {
+    sup_go<R, S, VEC && sizeof(R) == 4>(grd, st, V, vstride, coef, x, act, n, recur, xzero);
+  }
+};
+
 template <typename R>
 void launch_gram(const cplx<R>* V, size_t vstride, int s, const int* act, int na, size_t n, const Epi& e,
                  cudaStream_t st) {
-  if (na <= 0) return;
-  const int nblk = reduction_blocks(na, n, GS_THREADS);
-  const size_t chunk = (n + nblk - 1) / nblk;
+  if (na <= 0 || s < 1 || s > SSTEP_MAX) return;
+  const bool vec = use_pairs<R>(V, vstride, V);
+  const int nblk = reduction_blocks(na, vec ? n / 2 + 1 : n, GS_THREADS);
+  const size_t units = vec ? n / 2 : n;
+  const size_t chunk = (units + nblk - 1) / nblk;
   dim3 grd(nblk, na);
-  ProfScope ps(prof_gs_class<R>(n), (double)(s + 1) * na * n * sizeof(cplx<R>), st);
-  switch (s) {
-    case 1: gram_go<R, 1>(grd, st, V, vstride, act, n, chunk, e); break;
-    case 2: gram_go<R, 2>(grd, st, V, vstride, act, n, chunk, e); break;
-    case 3: gram_go<R, 3>(grd, st, V, vstride, act, n, chunk, e); break;
-    case 4: gram_go<R, 4>(grd, st, V, vstride, act, n, chunk, e); break;
-    case 5: gram_go<R, 5>(grd, st, V, vstride, act, n, chunk, e); break;
-    case 6: gram_go<R, 6>(grd, st, V, vstride, act, n, chunk, e); break;
-    case 7: gram_go<R, 7>(grd, st, V, vstride, act, n, chunk, e); break;
-    default: gram_go<R, 8>(grd, st, V, vstride, act, n, chunk, e); break;
-  }
+  ProfScope ps(prof_gs_class<R>(n, PC_GRAM32), (double)(s + 1) * na * n * sizeof(cplx<R>), st);
+  s_dispatch<R, GramGo>(s, vec, grd, st, V, vstride, act, n, chunk, e);
+  count_launch();
+}
+
+template <typename R>
+void launch_sstep_update(cplx<R>* V, size_t vstride, int s, const cplx<R>* coef, cplx<R>* x, const int* act, int na,
+                         size_t n, int recur, int xzero, cudaStream_t st) {
+  if (na <= 0 || s < 1 || s > SSTEP_MAX) return;
+  const bool vec = use_pairs<R>(V, vstride, x);
+  const size_t units = vec ? n / 2 + 1 : n;
+  const int per_slot = std::max(1, std::min((int)((units + GS_THREADS - 1) / GS_THREADS), (152 * 8 + na - 1) / na));
+  dim3 grd(per_slot, na);
+  // bytes: W_0..W_{s-1} (and W_s) read, x read unless zero, x written (and W_0)
+  const double vecs = s + (recur ? 2 : 0) + (xzero ? 1 : 2);
+  ProfScope ps(prof_gs_class<R>(n, PC_UPDATE32), vecs * na * n * sizeof(cplx<R>), st);
+  s_dispatch<R, SupGo>(s, vec, grd, st, V, vstride, coef, x, act, n, recur, xzero);
   count_launch();
 }
 
@@ -260,6 +443,10 @@ template void launch_gs<float>(int, const float2*, size_t, int, const float2*, c
                                const int*, int, size_t, const Epi&, cudaStream_t);
 template void launch_gs<double>(int, const double2*, size_t, int, const double2*, const double2*, Scale<double>,
                                 double2*, const int*, int, size_t, const Epi&, cudaStream_t);
+template void launch_sstep_update<float>(float2*, size_t, int, const float2*, float2*, const int*, int, size_t,
+                                         int, int, cudaStream_t);
+template void launch_sstep_update<double>(double2*, size_t, int, const double2*, double2*, const int*, int, size_t,
+                                          int, int, cudaStream_t);
 template void launch_gram<float>(const float2*, size_t, int, const int*, int, size_t, const Epi&, cudaStream_t);
 template void launch_gram<double>(const double2*, size_t, int, const int*, int, size_t, const Epi&, cudaStream_t);
 template void launch_zero<float>(float2*, const int*, int, size_t, cudaStream_t);

@@ -362,19 +362,27 @@ static int krylov(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x
 // the same Krylov space): W_0 = r = bs*b - H x, W_i = H W_{i-1} for i = 1..k,
 // one Gram pass over W_0..W_k, the k x k normal equations in FP64 (diagonally
 // scaled, so the basis needs no normalisation), x += sum_i y_i W_i.  A cycle
-// streams k+3 passes instead of the ~k^2 of Gram-Schmidt.
+// streams k+3 passes instead of the ~k^2 of Gram-Schmidt.  Between cycles the
+// next residual comes by recurrence, r = W_0 - sum_i y_i W_{i+1}, in the same
+// pass as the update of x, so only the first cycle applies the stencil to x.
+// With want_resid the last cycle also leaves that residual in W_0 and the
+// function returns it (nullptr otherwise).
 template <typename R>
-static void sstep(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero, int cycles) {
+static const cplx<R>* sstep(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero,
+                            int cycles, bool want_resid) {
   const OpView<R> op = op_view<R>(c, I.level, c.dir);
   const size_t n = op.n;
   const size_t vs = (size_t)c.B * n;
   const int S = I.k;
+  if (cycles <= 0) {
+    if (x0_zero) launch_zero<R>(x, c.act, c.na, n, c.st);
+    return nullptr;
+  }
   for (int cyc = 0; cyc < cycles && c.na > 0; ++cyc) {
     if (cyc == 0 && x0_zero) {
       // x = 0: the residual is bs*b itself; the first image is H(bs*b)
-      launch_zero<R>(x, c.act, c.na, n, c.st);
       launch_gs<R>(GS_ADD_STORE, nullptr, 0, 0, nullptr, b, bs, I.V, c.act, c.na, n, Epi{}, c.st);
-    } else {
+    } else if (cyc == 0) {
       launch_stencil<R>(op, c.slot_f, c.act, c.na, x, Scale<R>{}, b, bs, I.V, c.st);
     }
     for (int i = 1; i <= S; ++i)
@@ -383,18 +391,23 @@ static void sstep(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x
     Epi eg = make_epi(c, EPI_GRAM, &I.ks);
     eg.idx = S;
     launch_gram<R>(I.V, vs, S, c.act, c.na, n, eg, c.st);
-    launch_gs<R>(GS_ADD_STORE, I.V, vs, S, (const cplx<R>*)I.ks.coef, x, Scale<R>{}, x, c.act, c.na, n, Epi{}, c.st);
+    const bool recur = cyc + 1 < cycles || want_resid;
+    launch_sstep_update<R>(I.V, vs, S, (const cplx<R>*)I.ks.coef, x, c.act, c.na, n, recur ? 1 : 0,
+                           (cyc == 0 && x0_zero) ? 1 : 0, c.st);
   }
+  return want_resid ? I.V : nullptr;
 }
 
 // A fixed-cycle solve without preconditioner (smoother or last-level coarse
-// solve): s-step cycles when enabled, Arnoldi otherwise.
+// solve): s-step cycles when enabled, Arnoldi otherwise.  With want_resid the
+// s-step path returns the residual bs*b - H x it carries (nullptr when the
+// caller has to form it).
 template <typename R>
-static void fixed_solve(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero, int cycles) {
-  if (c.P->o.sstep && I.k <= SSTEP_MAX)
-    sstep<R>(c, I, b, bs, x, x0_zero, cycles);
-  else
-    krylov<R>(c, I, b, bs, x, x0_zero, cycles, 0.0, nullptr, nullptr);
+static const cplx<R>* fixed_solve(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x, bool x0_zero,
+                                  int cycles, bool want_resid = false) {
+  if (c.P->o.sstep && I.k <= SSTEP_MAX) return sstep<R>(c, I, b, bs, x, x0_zero, cycles, want_resid);
+  krylov<R>(c, I, b, bs, x, x0_zero, cycles, 0.0, nullptr, nullptr);
+  return nullptr;
 }
 
 // ML-GMRES V-cycle at `level`: out = M^{-1}(ins*in), zero initial guess.
@@ -406,11 +419,14 @@ static void vcycle(Ctx& c, int level, const cplx<R>* in, Scale<R> ins, cplx<R>* 
   KInst<R>& smooth = H.inst[level == 0 ? 1 : 3];
   KInst<R>& coarse = H.inst[level == 0 ? 2 : 4];
   const OpView<R> op = op_view<R>(c, level, c.dir);
-  // pre-smoothing from zero
-  fixed_solve<R>(c, smooth, in, ins, out, true, o.k_so);
-  // residual, restriction
-  launch_stencil<R>(op, c.slot_f, c.act, c.na, out, Scale<R>{}, in, ins, H.r[level], c.st);
-  launch_restrict<R>(H.r[level], P.lev[level], H.b[level + 1], P.lev[level + 1], c.act, c.na, c.st);
+  // pre-smoothing from zero; the residual (carried by the s-step smoother, or
+  // formed here) is restricted to the next level
+  const cplx<R>* r = fixed_solve<R>(c, smooth, in, ins, out, true, o.k_so, true);
+  if (!r) {
+    launch_stencil<R>(op, c.slot_f, c.act, c.na, out, Scale<R>{}, in, ins, H.r[level], c.st);
+    r = H.r[level];
+  }
+  launch_restrict<R>(r, P.lev[level], H.b[level + 1], P.lev[level + 1], c.act, c.na, c.st);
   // coarse solve, recursively preconditioned except on the last level
   if (level + 1 < P.L - 1) {
     typename PrecT<R>::T pc = [&c, level](const cplx<R>* i2, Scale<R> s2, cplx<R>* o2) {

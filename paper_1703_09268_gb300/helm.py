@@ -23,7 +23,7 @@ FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
 CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT = 0, 1, 2, 3, 4, 5
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
-                "misc", "stencil_c64_coarse", "krylov_c64_coarse"]
+                "misc", "stencil_c64_coarse", "krylov_c64_coarse", "gram_c64", "update_c64"]
 
 
 class HelmGrid(ctypes.Structure):
