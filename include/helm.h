@@ -59,7 +59,7 @@ typedef enum {
   HELM_E_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
   HELM_E_NOCONV = -4,    /* some solve missed its tolerance (outputs written) */
   HELM_E_NONFINITE = -5, /* NaN/Inf met in a residual */
-  HELM_E_TIMEOUT = -6    /* reserved: a bounded device wait expired */
+  HELM_E_TIMEOUT = -6    /* a kernel gave up on a bounded wait for its bulk copies; outputs are void */
 } helm_status;
 
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;

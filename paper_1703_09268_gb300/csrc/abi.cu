@@ -183,6 +183,7 @@ static void fill_reports(helm_rhs_report* reports, const std::vector<int>& g,
 
 static int worst(int a, int b) {
   if (a == HELM_E_CUDA || b == HELM_E_CUDA) return HELM_E_CUDA;
+  if (a == HELM_E_TIMEOUT || b == HELM_E_TIMEOUT) return HELM_E_TIMEOUT;
   if (a == HELM_E_NONFINITE || b == HELM_E_NONFINITE) return HELM_E_NONFINITE;
   if (a == HELM_E_NOCONV || b == HELM_E_NOCONV) return HELM_E_NOCONV;
   return a != HELM_OK ? a : b;
@@ -311,14 +312,14 @@ int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int
                    c.slot_s, nb, c.q, c.err + 1, c.st);
     std::vector<SlotReport> rep;
     st = solve_batch(c, 0, c.q, c.u, nb, rep);
-    if (st == HELM_E_CUDA) return st;
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     for (auto& r : rep) result = worst(result, r.status);
     if (U_out) launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
     if (D_out) launch_receivers(*P, c.u, rec_idx, nrec, c.slot_g, nb, (double2*)D_out, nrec, c.st);
     fill_reports(reports, g, rep);
   }
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -344,13 +345,13 @@ int helm_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz, int
     launch_spread(*P, (const double2*)R_in, nrec, rec_idx, nrec, 1.0, c.slot_g, nb, c.q, c.st);
     std::vector<SlotReport> rep;
     st = solve_batch(c, 1, c.q, c.v, nb, rep);
-    if (st == HELM_E_CUDA) return st;
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     for (auto& r : rep) result = worst(result, r.status);
     launch_copy_fields(c.v, (double2*)V_out, c.ident, nb, c.slot_g, n, c.st);
     fill_reports(reports, g, rep);
   }
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -374,7 +375,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
   if (mask) {
     std::vector<uint8_t> mh(nrhs);
     cudaMemcpyAsync(mh.data(), mask, nrhs, cudaMemcpyDeviceToHost, c.st);
-    if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+    if (const int sc = sync_check(c); sc != HELM_OK) return sc;
     for (int i = 0; i < nrhs; ++i)
       if (mh[i]) todo.push_back(i);
   } else {
@@ -395,7 +396,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
                    c.slot_s, nb, c.q, c.err + 1, c.st);
     std::vector<SlotReport> rf, ra;
     st = solve_batch(c, 0, c.q, c.u, nb, rf);
-    if (st == HELM_E_CUDA) return st;
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     // misfit and adjoint source -P_r^T (P_r u - d)
     launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.slot_f, c.slot_s, nsrc, c.ident,
@@ -405,7 +406,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
     launch_spread(*P, c.res, nrec, rec_idx, nrec, -1.0, c.ident, nb, c.q, c.st);
     // adjoint state v = H^{-H} b
     st = solve_batch(c, 1, c.q, c.v, nb, ra);
-    if (st == HELM_E_CUDA) return st;
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     // g += w^2 Re(conj(u) v)
     launch_grad_accum(c.u, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
@@ -421,7 +422,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
     fill_reports(reports, g, rf);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -434,7 +435,7 @@ static int mask_list(Ctx& c, const uint8_t* mask, int nrhs, std::vector<int>& to
   }
   std::vector<uint8_t> mh(nrhs);
   cudaMemcpyAsync(mh.data(), mask, nrhs, cudaMemcpyDeviceToHost, c.st);
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   for (int i = 0; i < nrhs; ++i)
     if (mh[i]) todo.push_back(i);
   return HELM_OK;
@@ -469,7 +470,7 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
                    c.q, c.err + 1, c.st);
     std::vector<SlotReport> rep;
     st = solve_batch(c, 0, c.q, c.u, nb, rep);
-    if (st == HELM_E_CUDA) return st;
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     for (auto& r : rep) result = worst(result, r.status);
     launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.slot_f, c.slot_s, nsrc, c.ident, nb,
@@ -479,7 +480,7 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
     if (U_out) launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
     fill_reports(reports, g, rep);
   }
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -510,14 +511,14 @@ int helm_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, in
     launch_spread(*P, (const double2*)R_in, nrec, rec_idx, nrec, -1.0, c.slot_g, nb, c.q, c.st);
     std::vector<SlotReport> rep;
     st = solve_batch(c, 1, c.q, c.v, nb, rep);
-    if (st == HELM_E_CUDA) return st;
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     for (auto& r : rep) result = worst(result, r.status);
     launch_grad_accum((const double2*)U_in, c.slot_g, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
     fill_reports(reports, g, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   return result;
 }
 

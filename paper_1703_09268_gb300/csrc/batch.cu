@@ -13,7 +13,7 @@
 #include "helm.h"
 
 static int worst_status(int a, int b) {
-  const int order[] = {HELM_E_CUDA, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_NONFINITE, HELM_E_NOCONV, HELM_E_TIMEOUT};
+  const int order[] = {HELM_E_CUDA, HELM_E_TIMEOUT, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_NONFINITE, HELM_E_NOCONV};
   for (int s : order)
     if (a == s || b == s) return s;
   return HELM_OK;

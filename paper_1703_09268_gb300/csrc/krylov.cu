@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace helm {
 
@@ -210,6 +211,104 @@ k_gram(const cplx<R>* __restrict__ V, size_t vstride, const int* __restrict__ ac
   epi_arrive<R>(e, a, s, gridDim.x, NV);
 }
 
+// Gram pass with the basis streamed into shared memory by bulk asynchronous
+// copies (TMA): a ring of GRAM_STAGES tiles of GS_THREADS point pairs per
+// vector, each tile announced on its own mbarrier.  Thread 0 keeps the ring
+// full while all threads reduce the tile in front; memory traffic and the
+// arithmetic (about 4.5 flops per byte) overlap instead of alternating.
+// Single precision, pairs of points (the same layout conditions as the paired
+// kernels).  A wait that gives up sets e.fault and the block stops streaming
+// (its sums are void; the call reports HELM_E_TIMEOUT).
+template <int S> __host__ __device__ constexpr int gram_stages() {
+  return (S + 1) * 4096 * 4 <= 100 * 1024 ? 4 : (S + 1) * 4096 * 3 <= 100 * 1024 ? 3 : 2;
+}
+template <int S> __host__ __device__ constexpr size_t gram_tma_smem() { return (size_t)gram_stages<S>() * (S + 1) * GS_THREADS * 16; }
+
+template <int S>
+__global__ void __launch_bounds__(GS_THREADS, 2)
+k_gram_tma(const float2* __restrict__ V, size_t vstride, const int* __restrict__ act, size_t n, size_t chunk,
+           Epi e) {
+  constexpr int NV = gram_nvals(S);
+  constexpr int ST = gram_stages<S>();
+  constexpr int TP = GS_THREADS;
+  extern __shared__ __align__(128) float4 ring[];  // [ST][S+1][TP]
+  __shared__ __align__(8) uint64_t full[ST];
+  const int a = blockIdx.y;
+  const int s = act[a];
+  const int tid = threadIdx.x;
+  const float2* Vs = V + (size_t)s * n;
+  const PairSplit sp = pair_split((size_t)s * n, n);
+  const size_t beg = min(sp.npair, (size_t)blockIdx.x * chunk);
+  const size_t end = min(sp.npair, beg + chunk);
+  const int ntile = (int)((end - beg + TP - 1) / TP);
+  if (tid == 0) {
+    for (int st = 0; st < ST; ++st) mbar_init(&full[st], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int t) {  // thread 0: tile t into stage t % ST
+    const int st = t % ST;
+    const size_t q0 = beg + (size_t)t * TP;
+    const uint32_t bytes = (uint32_t)min((size_t)TP, end - q0) * 16u;
+    mbar_arrive_expect_tx(&full[st], bytes * (S + 1));
+#pragma unroll
+    for (int i = 0; i <= S; ++i)
+      bulk_g2s(ring + ((size_t)st * (S + 1) + i) * TP, Vs + i * vstride + sp.head + 2 * q0, bytes, &full[st]);
+  };
+  if (tid == 0)
+    for (int t = 0; t < min(ST, ntile); ++t) issue(t);
+  float acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.f;
+  int done = 0;  // tiles consumed
+  bool failed = false;
+  for (int t = 0; t < ntile; ++t) {
+    const int st = t % ST;
+    const bool ok = mbar_wait_bounded(&full[st], (uint32_t)(t / ST) & 1u);
+    // one barrier per tile: everyone has left tile t-1 (its stage may be
+    // refilled) and agrees on whether tile t arrived
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0 && t >= 1 && t - 1 + ST < ntile) issue(t - 1 + ST);
+    const size_t q0 = beg + (size_t)t * TP;
+    if (q0 + tid < end) {
+      float2 wa[S + 1], wb[S + 1];
+#pragma unroll
+      for (int i = 0; i <= S; ++i) {
+        const float4 v = ring[((size_t)st * (S + 1) + i) * TP + tid];
+        wa[i] = make_float2(v.x, v.y);
+        wb[i] = make_float2(v.z, v.w);
+      }
+      gram_point<float, S>(wa, acc);
+      gram_point<float, S>(wb, acc);
+    }
+    done = t + 1;
+  }
+  if (failed && tid == 0) {
+    if (e.fault) atomicExch(e.fault, 1);
+    // let the copies already issued land (bounded) before the block exits
+    const int issued = min(ntile, max(ST, done + ST - 1));
+    for (int t = done; t < issued; ++t) (void)mbar_wait_bounded(&full[t % ST], (uint32_t)(t / ST) & 1u);
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    float2 w[S + 1];
+    if (sp.head) {
+#pragma unroll
+      for (int i = 0; i <= S; ++i) w[i] = Vs[i * vstride];
+      gram_point<float, S>(w, acc);
+    }
+    if (sp.tail) {
+#pragma unroll
+      for (int i = 0; i <= S; ++i) w[i] = Vs[i * vstride + n - 1];
+      gram_point<float, S>(w, acc);
+    }
+  }
+  block_partial_row<float, NV, GS_THREADS / 32>(acc, NV, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * NV);
+  epi_arrive<float>(e, a, s, gridDim.x, NV);
+}
+
 // End of an s-step cycle: x += sum_{i<S} y_i W_i (x = sum_i y_i W_i when
 // xzero), and with recur the next residual by recurrence in the same pass,
 // W_0 <- W_0 - sum_{i<S} y_i W_{i+1} (= b - H x_new since W_{i+1} = H W_i).
@@ -373,7 +472,19 @@ static void s_dispatch(int s, bool vec, A&&... args) {
 template <typename R, int S, bool VEC> struct GramGo {
   static void go(dim3 grd, cudaStream_t st, const cplx<R>* V, size_t vstride, const int* act, size_t n, size_t chunk,
                  const Epi& e) {
-    gram_go<R, S, VEC && sizeof(R) == 4>(grd, st, V, vstride, act, n, chunk, e);
+    if constexpr (VEC && sizeof(R) == 4) {
+      // dynamic shared memory above 48 KB is opt-in, once per kernel and device
+      static std::atomic<bool> attr[64];
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64 || !attr[dev].load(std::memory_order_acquire)) {
+        cudaFuncSetAttribute(k_gram_tma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_tma_smem<S>());
+        if (dev >= 0 && dev < 64) attr[dev].store(true, std::memory_order_release);
+      }
+      k_gram_tma<S><<<grd, GS_THREADS, gram_tma_smem<S>(), st>>>((const float2*)V, vstride, act, n, chunk, e);
+    } else {
+      gram_go<R, S, false>(grd, st, V, vstride, act, n, chunk, e);
+    }
   }
 };
 template <typename R, int S, bool VEC> struct SupGo {

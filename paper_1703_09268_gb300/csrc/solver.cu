@@ -179,7 +179,16 @@ template <> OpView<double> op_view<double>(const Ctx& c, int level, int dir) {
 int sync_check(Ctx& c) {
   cudaError_t e = cudaStreamSynchronize(c.st);
   if (e == cudaSuccess) e = cudaGetLastError();
-  return e == cudaSuccess ? HELM_OK : HELM_E_CUDA;
+  if (e != cudaSuccess) return HELM_E_CUDA;
+  if (c.err) {
+    // err[3]: a kernel gave up on a bounded wait (results of the call are void)
+    int gave_up = 0;
+    if (cudaMemcpyAsync(&gave_up, c.err + 3, sizeof(int), cudaMemcpyDeviceToHost, c.st) != cudaSuccess ||
+        cudaStreamSynchronize(c.st) != cudaSuccess)
+      return HELM_E_CUDA;
+    if (gave_up) return HELM_E_TIMEOUT;
+  }
+  return HELM_OK;
 }
 
 void set_active(Ctx& c, const std::vector<int>& a) {
@@ -244,6 +253,7 @@ static Epi make_epi(Ctx& c, int kind, const KState* ks = nullptr) {
   if (ks) e.ks = *ks;
   e.counter = c.counter;
   e.partial = c.partial;
+  e.fault = c.err ? c.err + 3 : nullptr;
   return e;
 }
 
@@ -296,7 +306,7 @@ static int krylov(Ctx& c, KInst<R>& I, const cplx<R>* b, Scale<R> bs, cplx<R>* x
     if (tol > 0.0) {
       cudaMemcpyAsync(rn.data(), I.ks.rnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
       cudaMemcpyAsync(bn.data(), I.ks.bnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
-      if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+      if (const int sc = sync_check(c); sc != HELM_OK) return sc;
       std::vector<int> keep;
       for (int s : c.act_h) {
         if (!std::isfinite(rn[s])) { status = HELM_E_NONFINITE; continue; }
@@ -501,7 +511,7 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
     for (int it = 0; it <= o.max_refine; ++it) {
       cudaMemcpyAsync(rn.data(), c.nrm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
       cudaMemcpyAsync(qn.data(), c.qn, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
-      if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+      if (const int sc = sync_check(c); sc != HELM_OK) return sc;
       std::vector<int> keep;
       for (int s : c.act_h) {
         if (!std::isfinite(rn[s])) { st = HELM_E_NONFINITE; continue; }
@@ -526,7 +536,7 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
       launch_stencil<double>(op64, c.slot_f, c.act, c.na, u, Scale<double>{}, q, Scale<double>{}, c.r64, c.st, &en);
     }
   }
-  if (sync_check(c) != HELM_OK) return HELM_E_CUDA;
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
   for (int a = 0; a < nb; ++a) {
     rep[a].iters = ko.iters[a];
     rep[a].rel = qn[a] > 0.0 ? rn[a] / qn[a] : 0.0;
