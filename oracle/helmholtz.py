@@ -18,7 +18,9 @@ Environment for Nonlinear Inverse Problems"):
     frequencies of Re(T(U)^H V), mapped back to the physical grid by the
     adjoint of the extension (to_phys);
   * Sec. 4 (Alg. vcycle text): linear-interpolation prolongation and its
-    adjoint as restriction (transfer operators only).
+    adjoint as restriction; the ML-GMRES V-cycle (GMRES smoothers, coarse
+    FGMRES, rediscretised coarse operators) and damped Jacobi as
+    preconditioners.
 
 Readings taken where the paper is silent (each also listed in the design doc):
   * m = 1/v^2 and H = L_eta + w^2 diag(m);
@@ -30,7 +32,10 @@ Readings taken where the paper is silent (each also listed in the design doc):
   * sources and receivers sit on grid nodes: the windowed-sinc operators of
     Sec. 3 reduce to point sampling; a unit source is 1/h^dim at its node;
   * extra high-side layer cells ("pad") make (N+1) divisible by 2^(levels-1)
-    for vertex-centred coarsening.
+    for vertex-centred coarsening;
+  * the V-cycle's "x~ <- x_f + P x_c" is x~ <- x~ + P x_c, the cycle starts
+    from x = 0, the coarse m is the full-weighting restriction of the fine m and
+    the coarse damping tables sample the same continuous sigma(x).
 
 Every array here is complex128 / float64.
 """
@@ -482,3 +487,153 @@ def prolongation(fine_N: Sequence[int], dim: int) -> sp.csr_matrix:
 def restriction(fine_N: Sequence[int], dim: int) -> sp.csr_matrix:
     """R = 2^-dim P^T."""
     return sp.csr_matrix(prolongation(fine_N, dim).T) * (0.5 ** dim)
+
+
+# ---------------------------------------------------------------------------
+# The ML-GMRES preconditioner (Sec. 4): rediscretised coarse operators, fixed
+# restarted GMRES / FGMRES cycles as smoothers and coarse solvers, the V-cycle;
+# and the damped Jacobi alternative
+# ---------------------------------------------------------------------------
+
+def level_N(g: Grid, level: int) -> tuple:
+    """Nodes per axis (x, y, z) at grid level `level` (vertex-centred coarsening,
+    N_c = (N - 1) / 2 on every active axis)."""
+    N = list(g.N)
+    for _ in range(level):
+        N = [N[d] if (g.dim == 2 and d == 1) else (N[d] - 1) // 2 for d in range(3)]
+    return tuple(N)
+
+
+def level_axis_coefficients(g: Grid, d: int, omega: float, level: int):
+    """The stretched second derivative of axis_coefficients rediscretised at
+    level `level`: spacing 2^level h; coarse node j sits on fine node
+    (j + 1) 2^level - 1, its half nodes 2^(level-1) fine cells either side, and
+    the damping profile is the same continuous sigma(x) of the finest grid."""
+    q = 1 << level
+    Nl = level_N(g, level)[d]
+    t = (np.arange(Nl, dtype=np.float64) + 1.0) * q - 1.0
+    a = 1.0 / (1.0 + 1j * sigma_at(t, d, g) / omega)
+    b_minus = 1.0 / (1.0 + 1j * sigma_at(t - 0.5 * q, d, g) / omega)
+    b_plus = 1.0 / (1.0 + 1j * sigma_at(t + 0.5 * q, d, g) / omega)
+    hl = q * g.h
+    cm = a * b_minus / (hl * hl)
+    cp = a * b_plus / (hl * hl)
+    return cm, cp, -(cm + cp)
+
+
+def level_models(g: Grid, m_comp: np.ndarray, levels: int) -> list:
+    """m on every level: the finest computational m, then full weighting
+    (R = 2^-dim P^T) of the level above."""
+    ms = [np.asarray(m_comp, dtype=np.float64).ravel()]
+    for l in range(1, levels):
+        R = restriction(level_N(g, l - 1), g.dim)
+        ms.append(R @ ms[-1])
+    return ms
+
+
+def level_matrix(g: Grid, m_level: np.ndarray, omega: float, level: int) -> sp.csr_matrix:
+    """H_level = sum_d L_d(level) + omega^2 diag(m_level) (same Kronecker
+    layout as helmholtz_matrix, which is level 0)."""
+    Nx, Ny, Nz = level_N(g, level)
+    Ix, Iy, Iz = (sp.identity(k, dtype=np.complex128, format="csr") for k in (Nx, Ny, Nz))
+    Lx = second_difference_1d(*level_axis_coefficients(g, 0, omega, level))
+    Lz = second_difference_1d(*level_axis_coefficients(g, 2, omega, level))
+    H = sp.kron(Iz, sp.kron(Iy, Lx)) + sp.kron(Lz, sp.kron(Iy, Ix))
+    if g.dim == 3:
+        Ly = second_difference_1d(*level_axis_coefficients(g, 1, omega, level))
+        H = H + sp.kron(Iz, sp.kron(Ly, Ix))
+    H = H + sp.diags(omega * omega * np.asarray(m_level, dtype=np.float64).ravel())
+    return sp.csr_matrix(H)
+
+
+def gmres_cycles(A, b: np.ndarray, k: int, cycles: int, x0: Optional[np.ndarray] = None,
+                 M=None) -> np.ndarray:
+    """`cycles` restarts of k steps of GMRES (M None) or flexible GMRES with the
+    right preconditioner z = M(v) (Saad's FGMRES, used by Sec. 4 for the
+    coarse solves), no stopping test: the fixed-work smoother / coarse solver.
+
+    Arnoldi with modified Gram-Schmidt and one re-orthogonalisation pass; the
+    least-squares problem min || beta e_1 - Hbar y || solved by a dense
+    least-squares routine; x += V y (or Z y)."""
+    b = np.asarray(b, dtype=np.complex128)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128)
+    for _ in range(cycles):
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta == 0.0:
+            break
+        V = np.zeros((k + 1, b.size), dtype=np.complex128)
+        Z = np.zeros((k, b.size), dtype=np.complex128) if M is not None else None
+        Hh = np.zeros((k + 1, k), dtype=np.complex128)
+        V[0] = r / beta
+        used = 0
+        for j in range(k):
+            zj = V[j] if M is None else M(V[j])
+            if Z is not None:
+                Z[j] = zj
+            w = A @ zj
+            for _pass in range(2):
+                for i in range(j + 1):
+                    hij = np.vdot(V[i], w)
+                    Hh[i, j] += hij
+                    w = w - hij * V[i]
+            Hh[j + 1, j] = np.linalg.norm(w)
+            used = j + 1
+            if Hh[j + 1, j] == 0.0:
+                break
+            V[j + 1] = w / Hh[j + 1, j]
+        e1 = np.zeros(used + 1, dtype=np.complex128)
+        e1[0] = beta
+        y = np.linalg.lstsq(Hh[:used + 1, :used], e1, rcond=None)[0]
+        x = x + (V[:used] if Z is None else Z[:used]).T @ y
+    return x
+
+
+class MLGmres:
+    """The ML-GMRES V-cycle of Sec. 4 as a preconditioner z = M^{-1} b.
+
+    Levels l = 0..L-1 with H_l rediscretised at spacing 2^l h (restricted m);
+    transfers P (linear interpolation) and R = 2^-dim P^T.  One cycle at level
+    l from a zero guess: pre-smooth with k_so cycles of GMRES(k_si), restrict
+    the residual, solve the coarse problem with k_co cycles of FGMRES(k_ci)
+    preconditioned by the level-(l+1) cycle (plain GMRES(k_ci) on the last
+    level), add the prolonged coarse solution, post-smooth as before.
+    adjoint=True builds the same cycle on the H_l^H."""
+
+    def __init__(self, g: Grid, m_comp, omega: float, levels: int = 2, k_so: int = 3, k_si: int = 5,
+                 k_co: int = 3, k_ci: int = 5, adjoint: bool = False):
+        self.g, self.L = g, levels
+        self.k_so, self.k_si, self.k_co, self.k_ci = k_so, k_si, k_co, k_ci
+        ms = level_models(g, m_comp, levels)
+        self.H = []
+        for l in range(levels):
+            H = level_matrix(g, ms[l], omega, l)
+            self.H.append(sp.csr_matrix(H.conj().T) if adjoint else H)
+        self.P = [prolongation(level_N(g, l), g.dim) for l in range(levels - 1)]
+        self.R = [restriction(level_N(g, l), g.dim) for l in range(levels - 1)]
+
+    def cycle(self, b: np.ndarray, level: int = 0) -> np.ndarray:
+        H = self.H[level]
+        x = gmres_cycles(H, b, self.k_si, self.k_so)
+        bc = self.R[level] @ (b - H @ x)
+        if level + 1 < self.L - 1:
+            xc = gmres_cycles(self.H[level + 1], bc, self.k_ci, self.k_co,
+                              M=lambda v: self.cycle(v, level + 1))
+        else:
+            xc = gmres_cycles(self.H[level + 1], bc, self.k_ci, self.k_co)
+        x = x + self.P[level] @ xc
+        return gmres_cycles(H, b, self.k_si, self.k_so, x0=x)
+
+    def __call__(self, b):
+        return self.cycle(np.asarray(b, dtype=np.complex128), 0)
+
+
+def jacobi_precond(H: sp.spmatrix, b: np.ndarray, omega_j: float, sweeps: int) -> np.ndarray:
+    """`sweeps` damped Jacobi sweeps z <- z + omega_j D^{-1} (b - H z) from z = 0,
+    D = diag(H) (the simple preconditioner alternative of Sec. 4)."""
+    b = np.asarray(b, dtype=np.complex128)
+    D = H.diagonal()
+    z = np.zeros_like(b)
+    for _ in range(sweeps):
+        z = z + omega_j * (b - H @ z) / D
+    return z

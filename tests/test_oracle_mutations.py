@@ -62,3 +62,75 @@ def test_pin_catches_conjugated_gradient(monkeypatch):
     monkeypatch.setattr(O, "DirectSolver", ConjAdjoint)
     with pytest.raises(AssertionError):
         T.test_gradient_matches_central_differences_2d()
+
+
+# ---------------------------------------------------------------------------
+# Preconditioner pins (tests/test_oracle_precond.py)
+# ---------------------------------------------------------------------------
+
+import tests.test_oracle_precond as TP  # noqa: E402
+
+
+def test_pin_catches_coarse_spacing_not_doubled(monkeypatch):
+    """Rediscretising the coarse level at spacing h instead of 2h."""
+    real = O.level_axis_coefficients
+
+    def fine_spacing(g, d, omega, level):
+        cm, cp, cd = real(g, d, omega, level)
+        f = float(1 << level) ** 2
+        return cm * f, cp * f, cd * f
+
+    monkeypatch.setattr(O, "level_axis_coefficients", fine_spacing)
+    with pytest.raises(AssertionError):
+        TP.test_coarse_operator_is_second_order_consistent()
+
+
+def test_pin_catches_coarse_node_offset(monkeypatch):
+    """Coarse node j placed on fine node 2j (instead of 2j+1) shifts the
+    damping profile; the smooth-field consistency check must fail."""
+    real_sigma = O.sigma_at
+
+    def shifted_level(g, d, omega, level):
+        q = 1 << level
+        Nl = O.level_N(g, level)[d]
+        t = np.arange(Nl, dtype=np.float64) * q
+        a = 1.0 / (1.0 + 1j * real_sigma(t, d, g) / omega)
+        bm = 1.0 / (1.0 + 1j * real_sigma(t - 0.5 * q, d, g) / omega)
+        bp = 1.0 / (1.0 + 1j * real_sigma(t + 0.5 * q, d, g) / omega)
+        hl = q * g.h
+        cm, cp = a * bm / hl ** 2, a * bp / hl ** 2
+        return cm, cp, -(cm + cp)
+
+    monkeypatch.setattr(O, "level_axis_coefficients", shifted_level)
+    with pytest.raises(AssertionError):
+        TP.test_coarse_operator_is_second_order_consistent()
+
+
+def test_pin_catches_subtracted_coarse_correction(monkeypatch):
+    """x <- x - P x_c (wrong sign of the coarse-grid correction)."""
+    real_prol = O.prolongation
+    monkeypatch.setattr(O, "prolongation", lambda N, dim: -real_prol(N, dim))
+    with pytest.raises(AssertionError):
+        TP.test_vcycle_is_an_effective_preconditioner(False)
+
+
+def test_pin_catches_unscaled_restriction(monkeypatch):
+    """R = P^T without the 2^-dim factor over-weights the coarse correction."""
+    real_prol = O.prolongation
+    monkeypatch.setattr(O, "restriction", lambda N, dim: real_prol(N, dim).T.tocsr())
+    with pytest.raises(AssertionError):
+        TP.test_vcycle_is_an_effective_preconditioner(False)
+
+
+def test_pin_catches_undamped_sign_flip_in_jacobi(monkeypatch):
+    """z <- z - w D^{-1}(b - H z) diverges from the solution."""
+    def wrong(H, b, omega_j, sweeps):
+        D = H.diagonal()
+        z = np.zeros_like(b)
+        for _ in range(sweeps):
+            z = z - omega_j * (b - H @ z) / D
+        return z
+
+    monkeypatch.setattr(O, "jacobi_precond", wrong)
+    with pytest.raises(AssertionError):
+        TP.test_jacobi_sweeps_converge_to_the_solution_on_a_dominant_diagonal()
