@@ -66,7 +66,7 @@ typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
 typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGMRES = 2 } helm_precond;
 typedef enum {
   HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
-  HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5
+  HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5, HELM_CALL_PRECOND = 6
 } helm_call;
 
 /* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
@@ -146,6 +146,24 @@ int helm_workspace_size(const helm_plan* plan, int call, int nfreq, int nsrc, in
 int helm_apply(helm_plan* plan, const double* m_phys, double freq_hz, int adjoint, int precision,
                const void* x, void* y, int nrhs, void* workspace, size_t ws_bytes,
                helm_stream_t stream);
+
+/* z = M^{-1} x: one application of the plan's preconditioner to each of
+ * `nrhs` fields at one frequency (Sec. 4): with HELM_PRECOND_MLGMRES one
+ * ML-GMRES V-cycle from a zero guess (pre-smoothing by k_so restarted cycles of
+ * GMRES(k_si), the residual restricted by full weighting, the rediscretised
+ * coarse problem at spacing 2h solved by k_co cycles of (F)GMRES(k_ci) --
+ * preconditioned by the next level's V-cycle when there is one -- its
+ * solution prolonged by linear interpolation and added, post-smoothing as
+ * before); with HELM_PRECOND_JACOBI `jacobi_sweeps` damped Jacobi sweeps from
+ * zero; with HELM_PRECOND_NONE a copy.  `adjoint` != 0 preconditions H^H
+ * instead (the same cycle on the adjoint operators).  Fields are in the
+ * plan's precision: complex128 [nrhs][n_comp] for HELM_FP64, complex64 for
+ * HELM_MIXED (the same types as helm_apply).  x is read only; z is written.
+ * The cycle is a nonlinear function of x when its smoothers are GMRES.
+ * Workspace: helm_workspace_size(plan, HELM_CALL_PRECOND, 1, nrhs, 0, ...);
+ * max_batch bounds the fields processed together. */
+int helm_precond_apply(helm_plan* plan, const double* m_phys, double freq_hz, int adjoint, const void* x,
+                       void* z, int nrhs, void* workspace, size_t ws_bytes, helm_stream_t stream);
 
 /* Forward modelling (Listing pdefunc, FORW_MODEL): for every frequency k and
  * source s solve H(m, w_k) u = q with q = wavelet[k] sum_j Q[j, s] delta_h(x - x_j),

@@ -244,7 +244,7 @@ int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys)
 
 int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
   if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
-  if (call < HELM_CALL_APPLY || call > HELM_CALL_GRADIENT) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_PRECOND) return HELM_E_INVAL;
   *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
   return HELM_OK;
 }
@@ -270,6 +270,26 @@ int helm_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, 
                           Scale<float>{}, nullptr, Scale<float>{}, (float2*)y, c.st);
   }
   return sync_check(c);
+}
+
+int helm_precond_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, const void* x, void* z,
+                       int nrhs, void* ws, size_t ws_bytes, helm_stream_t stream) {
+  if (!P || !m_phys || !x || !z || nrhs < 1 || !(freq_hz > 0.0) || !std::isfinite(freq_hz)) return HELM_E_INVAL;
+  Ctx c;
+  int st = bind(P, HELM_CALL_PRECOND, 1, nrhs, 0, ws, ws_bytes, stream, c);
+  if (st != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, &freq_hz)) != HELM_OK) return st;
+  const size_t n = P->lev[0].n;
+  const size_t esz = P->o.precision == HELM_MIXED ? sizeof(float2) : sizeof(double2);
+  for (int start = 0; start < nrhs; start += c.B) {
+    const int nb = std::min(c.B, nrhs - start);
+    std::vector<int> g(nb);
+    for (int a = 0; a < nb; ++a) g[a] = start + a;
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    st = precond_apply(c, adjoint ? 1 : 0, (const char*)x + (size_t)start * n * esz, (char*)z + (size_t)start * n * esz);
+    if (st != HELM_OK) return st;
+  }
+  return HELM_OK;
 }
 
 static int check_common(helm_plan* P, const double* m_phys, const double* freqs, int nfreq, int nsrc) {

@@ -57,11 +57,11 @@ static void layout_krylov(Bump& bp, KInst<R>& I, int level, int k, bool flex, in
 }
 
 template <typename R>
-static void layout_hierarchy(Bump& bp, const helm_plan& P, Hierarchy<R>& H, int B) {
+static void layout_hierarchy(Bump& bp, const helm_plan& P, Hierarchy<R>& H, int B, bool outer = true) {
   const helm_solve_opts& o = P.o;
   const size_t n0 = P.lev[0].n;
   const bool flex0 = o.precond != HELM_PRECOND_NONE;
-  layout_krylov<R>(bp, H.inst[0], 0, o.k_inner, flex0, B, n0);
+  if (outer) layout_krylov<R>(bp, H.inst[0], 0, o.k_inner, flex0, B, n0);
   if (o.precond == HELM_PRECOND_JACOBI) {
     H.r[0] = bp.take<cplx<R>>((size_t)B * n0);
   } else if (o.precond == HELM_PRECOND_MLGMRES) {
@@ -125,6 +125,12 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   C.partial = bp.take<double>((size_t)std::max(RED_BLOCKS_MAX, B) *
                               std::max(2 * (KMAX + 1), gram_nvals(SSTEP_MAX)));
   C.counter = bp.take<unsigned>(B);
+  if (call == HELM_CALL_PRECOND) {
+    // the preconditioner's own levels only (no outer basis, no FP64 fields)
+    if (C.mixed) layout_hierarchy<float>(bp, P, C.h32, B, false);
+    else layout_hierarchy<double>(bp, P, C.h64, B, false);
+    return bp.off;
+  }
   const size_t n0 = P.lev[0].n;
   C.q = bp.take<double2>((size_t)B * n0);
   C.u = bp.take<double2>((size_t)B * n0);
@@ -480,6 +486,27 @@ static int outer_solve(Ctx& c, const cplx<R>* b, cplx<R>* x, double tol, KrylovO
     pp = &pc;
   }
   return krylov<R>(c, H.inst[0], b, Scale<R>{}, x, true, o.max_cycles, tol, pp, ko, final_resid);
+}
+
+template <typename R>
+static void precond_apply_t(Ctx& c, const cplx<R>* x, cplx<R>* z) {
+  const helm_solve_opts& o = c.P->o;
+  if (o.precond == HELM_PRECOND_MLGMRES) {
+    vcycle<R>(c, 0, x, Scale<R>{}, z);
+  } else if (o.precond == HELM_PRECOND_JACOBI) {
+    jacobi<R>(c, x, Scale<R>{}, z);
+  } else {
+    cudaMemcpyAsync(z, x, sizeof(cplx<R>) * (size_t)c.na * c.P->lev[0].n, cudaMemcpyDeviceToDevice, c.st);
+  }
+}
+
+int precond_apply(Ctx& c, int dir, const void* x, void* z) {
+  c.dir = dir;
+  if (c.mixed)
+    precond_apply_t<float>(c, (const float2*)x, (float2*)z);
+  else
+    precond_apply_t<double>(c, (const double2*)x, (double2*)z);
+  return sync_check(c);
 }
 
 int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep) {

@@ -103,6 +103,9 @@ void set_active(Ctx& c, const std::vector<int>& a);
 // q and u are FP64 batch arrays.  Fills rep[0..nb-1].
 int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep);
 int sync_check(Ctx& c);
+// z = M^{-1} x for the active slots (the plan's preconditioner, the plan's
+// precision; dir 1 uses the adjoint operator H^H).
+int precond_apply(Ctx& c, int dir, const void* x, void* z);
 
 template <typename R> OpView<R> op_view(const Ctx& c, int level, int dir);
 

@@ -21,7 +21,8 @@ HELM_OK, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_CUDA, HELM_E_NOCONV, HELM_E_NONFINIT
     0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
-CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT = 0, 1, 2, 3, 4, 5
+CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT, CALL_PRECOND = \
+    0, 1, 2, 3, 4, 5, 6
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
                 "misc", "stencil_c64_coarse", "krylov_c64_coarse", "gram_c64", "update_c64"]
 
@@ -57,7 +58,7 @@ class HelmBatchItem(ctypes.Structure):
 
 
 EXPORTS = ["helm_default_opts", "helm_misfit_and_gradient_batch", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
-           "helm_workspace_size", "helm_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
+           "helm_workspace_size", "helm_apply", "helm_precond_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
            "helm_misfit", "helm_gradient",
            "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read"]
 
@@ -75,6 +76,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_plan_dims.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(S), ctypes.POINTER(S)]
     lib.helm_workspace_size.argtypes = [P, I, I, I, I, ctypes.POINTER(S)]
     lib.helm_apply.argtypes = [P, P, D, I, I, P, P, I, P, S, P]
+    lib.helm_precond_apply.argtypes = [P, P, D, I, P, P, I, P, S, P]
     lib.helm_forward.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, S,
                                  ctypes.POINTER(HelmRhsReport), P]
     lib.helm_adjoint.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, S,
@@ -249,6 +251,28 @@ def helm_apply(plan: Plan, m_phys: torch.Tensor, freq_hz: float, x: torch.Tensor
     _check(lib().helm_apply(plan._h, _ptr(m_phys), float(freq_hz), int(bool(adjoint)), prec, _ptr(x),
                             _ptr(y), nrhs, ws, nb, _stream(x.device)), "helm_apply")
     return y
+
+
+def helm_precond_apply(plan: Plan, m_phys: torch.Tensor, freq_hz: float, x: torch.Tensor, adjoint: bool = False,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """z = M^{-1} x (one V-cycle, Jacobi sweeps or a copy, as the plan's options
+    say) for x of shape (nrhs, n_comp): complex128 for an FP64 plan, complex64
+    for a mixed-precision plan."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _check_common(plan, m_phys)
+    want = torch.complex128 if plan.opts.precision == FP64 else torch.complex64
+    _need(x.dtype == want, f"x must be {want} for this plan's precision")
+    _dev(x, x.dtype, "x")
+    nrhs = x.numel() // plan.n_comp
+    if nrhs * plan.n_comp != x.numel():
+        raise ValueError("x must hold whole fields")
+    z = torch.empty_like(x) if out is None else out
+    _need(z.dtype == x.dtype and z.numel() == x.numel() and z.is_contiguous() and z.data_ptr() != x.data_ptr(),
+          "out must be a distinct contiguous tensor like x")
+    ws, nb = plan.workspace(plan.workspace_size(CALL_PRECOND, 1, nrhs, 0))
+    _check(lib().helm_precond_apply(plan._h, _ptr(m_phys), float(freq_hz), int(bool(adjoint)), _ptr(x), _ptr(z),
+                                    nrhs, ws, nb, _stream(x.device)), "helm_precond_apply")
+    return z
 
 
 def _reports(n):
