@@ -179,6 +179,22 @@ def _oracle_worker(args):
     return dict(iters=it_total, seconds=t_run, setup=t_setup)
 
 
+# DRAM traffic of the single-precision stencil from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_stencil_plain<float, 0>,
+# 16 fields of 85^3; profiles/stencil_c64_85cubed_16fields.md).  It scales with
+# the points a launch processes.  None when no capture matches the current
+# kernel.
+STENCIL_TRAFFIC = dict(kernel="k_stencil_plain<float, 0>", dram_bytes=81.167360e6 + 40.201216e6,
+                       algorithmic_bytes=16 * 614125 * 16 + 614125 * 4)
+
+
+def stencil_traffic(kernel_class, bytes_per_launch):
+    if kernel_class != "stencil_c64" or STENCIL_TRAFFIC is None:
+        return None
+    t = STENCIL_TRAFFIC
+    return round(t["dram_bytes"] * bytes_per_launch / t["algorithmic_bytes"], 1)
+
+
 def cpu_baseline(n, seconds):
     """(src.freq)/s of the oracle on the host cores: a bounded sample of GMRES
     iterations on the full-size operator in one spawned process per core,
@@ -368,8 +384,10 @@ def main():
     helm.profile_enable(True)
     flush.zero_()
     torch.cuda.synchronize()
+    t_prof = time.perf_counter()
     step(reduce=False)
     torch.cuda.synchronize()
+    wall_prof_ms = 1e3 * (time.perf_counter() - t_prof)
     prof = helm.profile_read()
     helm.profile_enable(False)
     hbm, hbm_kind = peaks()
@@ -383,7 +401,9 @@ def main():
                     bytes_per_launch=dn["bytes"] / max(dn["launches"], 1),
                     share={k: round(v["ms"] / tot_ms, 3) for k, v in prof.items() if v["launches"]},
                     class_frac={k: round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm, 3)
-                                for k, v in prof.items() if v["launches"] and v["bytes"] > 0 and v["ms"] > 0})
+                                for k, v in prof.items() if v["launches"] and v["bytes"] > 0 and v["ms"] > 0},
+                    gpu_busy=round(tot_ms / wall_prof_ms, 3))
+    roofline["traffic"] = stencil_traffic(dom, roofline["bytes_per_launch"])
     st = prof["stencil_c64"] if prof["stencil_c64"]["launches"] else prof["stencil_c128"]
     sbytes_pt = 16.0 if prof["stencil_c64"]["launches"] else 32.0
     stencil = dict(gpts=round(st["bytes"] / sbytes_pt / (st["ms"] / 1e3) / 1e9, 1),

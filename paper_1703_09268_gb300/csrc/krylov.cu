@@ -499,8 +499,11 @@ void launch_gram(const cplx<R>* V, size_t vstride, int s, const int* act, int na
                  cudaStream_t st) {
   if (na <= 0 || s < 1 || s > SSTEP_MAX) return;
   const bool vec = use_pairs<R>(V, vstride, V);
-  const int nblk = reduction_blocks(na, vec ? n / 2 + 1 : n, GS_THREADS);
   const size_t units = vec ? n / 2 : n;
+  // the streamed (paired) kernel holds two blocks per SM: one wave of them
+  int nblk = vec ? std::max(1, std::min((int)((units + GS_THREADS - 1) / GS_THREADS), 2 * 152 / na))
+                 : reduction_blocks(na, n, GS_THREADS);
+  if ((size_t)nblk * na > (size_t)RED_BLOCKS_MAX) nblk = std::max(1, RED_BLOCKS_MAX / na);
   const size_t chunk = (units + nblk - 1) / nblk;
   dim3 grd(nblk, na);
   ProfScope ps(prof_gs_class<R>(n, PC_GRAM32), (double)(s + 1) * na * n * sizeof(cplx<R>), st);

@@ -35,22 +35,32 @@ struct TileGeom {
 };
 
 // Plain apply (no reduction): one tile per block, grid (tiles, active slots).
+// The tile's z coefficients sit in shared memory and, in single precision,
+// the z march is fully unrolled (no register rotation between planes).
 template <typename R, bool RESID>
-__global__ void __launch_bounds__(STPB, sizeof(R) == 4 ? 10 : 6)
+__global__ void __launch_bounds__(STPB, 6)
 k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
                 const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
                 const R* __restrict__ m, const R* __restrict__ w2, const int* __restrict__ slot_f,
                 const int* __restrict__ act, TileGeom G) {
   using C = cplx<R>;
+  __shared__ C stz[3][ZRUN];
   const int planei = G.K0 * G.K1;
   const int seg = blockIdx.x % G.nseg;
   const int zc = blockIdx.x / G.nseg;
   const int p2 = seg * STPB + threadIdx.x;
-  if (p2 >= planei) return;
   const int s = act[blockIdx.y];
   const int f = slot_f[s];
   const C* T = tab + (size_t)f * 9 * G.Nmax;
   const C* Tz = T + 6 * G.Nmax;
+  const int z0 = zc * ZRUN;
+  const int z1 = min(z0 + ZRUN, G.K2);
+  if (threadIdx.x < 3 * ZRUN) {
+    const int k = threadIdx.x / ZRUN, zz = threadIdx.x % ZRUN;
+    stz[k][zz] = z0 + zz < G.K2 ? Tz[k * G.Nmax + z0 + zz] : mkc(R(0), R(0));
+  }
+  __syncthreads();
+  if (p2 >= planei) return;
   const R om2 = w2[f];
   const C* X = x + (size_t)s * G.n;
   C* Y = y + (size_t)s * G.n;
@@ -59,8 +69,6 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
   const C xm = T[ix], xd = T[G.Nmax + ix], xp = T[2 * G.Nmax + ix];
   const C ym = T[3 * G.Nmax + iy], yd = T[4 * G.Nmax + iy], yp = T[5 * G.Nmax + iy];
   const R dre = xd.x + yd.x, dim = xd.y + yd.y;
-  const int z0 = zc * ZRUN;
-  const int z1 = min(z0 + ZRUN, G.K2);
   // pointer stepping: xq/yq/mq address plane z of this column; neighbours are
   // fixed offsets from xq
   const int P = planei;
@@ -79,7 +87,10 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
   C next = (z0 + 1 < G.K2) ? xq[P] : zero;
   C w = hw ? xq[-1] : zero, ea = he ? xq[1] : zero, so = hs ? xq[-K0] : zero, no = hn ? xq[K0] : zero;
   R mm = mq[0];
-  for (int z = z0; z < z1; ++z) {
+#pragma unroll(sizeof(R) == 4 ? ZRUN : 1)
+  for (int zz = 0; zz < ZRUN; ++zz) {
+    const int z = z0 + zz;
+    if (z >= z1) break;
     const C* xn = xq + P;  // plane z+1
     C next2 = zero, w2n = zero, e2n = zero, s2n = zero, n2n = zero;
     R m2 = R(0);
@@ -91,7 +102,7 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
       n2n = hn ? xn[K0] : zero;
       m2 = mq[P];
     }
-    const C zm = Tz[z], zd = Tz[G.Nmax + z], zp = Tz[2 * G.Nmax + z];
+    const C zm = stz[0][zz], zd = stz[1][zz], zp = stz[2][zz];
     const C diag = mkc(dre + zd.x + om2 * mm, dim + zd.y);
     C h = cmul(diag, cur);
     h = cfma(xm, w, h);
