@@ -27,70 +27,99 @@ template <> __device__ __forceinline__ float2 add(float2 a, float2 b) { return m
 
 struct Dims { int f[3]; int c[3]; };
 
-// coarse = R fine for one slot per blockIdx.y (act list) or a single field (act == nullptr)
+// Grid of both kernels: (plane segments of 256 points, planes, slots); all
+// index arithmetic in 32 bits within a plane.
+
+// coarse = R fine for one slot per blockIdx.z (act list) or a single field (act == nullptr)
 template <typename T, typename W>
-__global__ void k_restrict(const T* __restrict__ fine, T* __restrict__ coarse, Dims D,
-                           const int* __restrict__ act, size_t nf, size_t nc) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nc) return;
-  const int s = act ? act[blockIdx.y] : 0;
-  const int jx = (int)(i % D.c[0]);
-  const int jy = (int)((i / D.c[0]) % D.c[1]);
-  const int jz = (int)(i / ((size_t)D.c[0] * D.c[1]));
-  const T* F = fine + (size_t)s * nf;
+__global__ void __launch_bounds__(256) k_restrict(const T* __restrict__ fine, T* __restrict__ coarse, Dims D,
+                                                  const int* __restrict__ act, size_t nf, size_t nc) {
+  const int Pc = D.c[0] * D.c[1];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Pc) return;
+  const int jz = blockIdx.y;
+  const int s = act ? act[blockIdx.z] : 0;
+  const int jx = q % D.c[0], jy = q / D.c[0];
   const bool cx = D.f[0] != D.c[0], cy = D.f[1] != D.c[1], cz = D.f[2] != D.c[2];
   const int fx = cx ? 2 * jx + 1 : jx, fy = cy ? 2 * jy + 1 : jy, fz = cz ? 2 * jz + 1 : jz;
+  const int Pf = D.f[0] * D.f[1];
+  const T* F = fine + (size_t)s * nf;
   T acc = zero_of<T>();
   const W w1[3] = {W(0.25), W(0.5), W(0.25)};
-  for (int dz = cz ? -1 : 0; dz <= (cz ? 1 : 0); ++dz) {
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    if (!cz && dz != 0) continue;
     const W wz = cz ? w1[dz + 1] : W(1);
-    for (int dy = cy ? -1 : 0; dy <= (cy ? 1 : 0); ++dy) {
+    const T* Fz = F + (size_t)(fz + dz) * Pf;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      if (!cy && dy != 0) continue;
       const W wy = cy ? w1[dy + 1] : W(1);
-      const size_t row = (size_t)D.f[0] * ((size_t)(fy + dy) + (size_t)D.f[1] * (size_t)(fz + dz));
-      for (int dx = cx ? -1 : 0; dx <= (cx ? 1 : 0); ++dx) {
+      const T* row = Fz + (fy + dy) * D.f[0] + fx;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!cx && dx != 0) continue;
         const W wx = cx ? w1[dx + 1] : W(1);
-        acc = axpy(acc, wx * wy * wz, F[row + fx + dx]);
+        acc = axpy(acc, wx * wy * wz, row[dx]);
       }
     }
   }
-  coarse[(size_t)s * nc + i] = acc;
+  coarse[(size_t)s * nc + (size_t)jz * Pc + q] = acc;
 }
 
-// fine += P coarse
+// fine += P coarse.  Every fine node takes two taps per coarsened axis (the
+// odd node's single parent appears once with weight 1, an even node's two
+// parents with 1/2 each, a missing parent beyond a wall with weight 0), so
+// lanes of a warp follow one path.
 template <typename T, typename W>
-__global__ void k_prolong_add(const T* __restrict__ coarse, T* __restrict__ fine, Dims D,
-                              const int* __restrict__ act, size_t nf, size_t nc) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nf) return;
-  const int s = act[blockIdx.y];
-  int f[3];
-  f[0] = (int)(i % D.f[0]);
-  f[1] = (int)((i / D.f[0]) % D.f[1]);
-  f[2] = (int)(i / ((size_t)D.f[0] * D.f[1]));
-  int idx[3][2];
-  W wt[3][2];
-  int cnt[3];
+__global__ void __launch_bounds__(256) k_prolong_add(const T* __restrict__ coarse, T* __restrict__ fine, Dims D,
+                                                     const int* __restrict__ act, size_t nf, size_t nc) {
+  const int Pf = D.f[0] * D.f[1];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Pf) return;
+  const int s = act[blockIdx.z];
+  const int fc[3] = {p % D.f[0], p / D.f[0], (int)blockIdx.y};
+  int i0[3], i1[3];
+  W w0[3], w1[3];
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
+    const int f = fc[d];
     if (D.f[d] == D.c[d]) {
-      cnt[d] = 1; idx[d][0] = f[d]; wt[d][0] = W(1);
-    } else if (f[d] & 1) {
-      cnt[d] = 1; idx[d][0] = (f[d] - 1) >> 1; wt[d][0] = W(1);
+      i0[d] = i1[d] = f;
+      w0[d] = W(1);
+      w1[d] = W(0);
+    } else if (f & 1) {
+      i0[d] = i1[d] = (f - 1) >> 1;
+      w0[d] = W(1);
+      w1[d] = W(0);
     } else {
-      cnt[d] = 0;
-      const int j = f[d] >> 1;  // neighbours j-1 and j
-      if (j - 1 >= 0) { idx[d][cnt[d]] = j - 1; wt[d][cnt[d]] = W(0.5); ++cnt[d]; }
-      if (j < D.c[d]) { idx[d][cnt[d]] = j; wt[d][cnt[d]] = W(0.5); ++cnt[d]; }
+      const int j = f >> 1;  // parents j-1 and j
+      i0[d] = j - 1 >= 0 ? j - 1 : 0;
+      i1[d] = j < D.c[d] ? j : D.c[d] - 1;
+      w0[d] = j - 1 >= 0 ? W(0.5) : W(0);
+      w1[d] = j < D.c[d] ? W(0.5) : W(0);
     }
   }
   const T* Cs = coarse + (size_t)s * nc;
+  const int Pc = D.c[0] * D.c[1];
   T acc = zero_of<T>();
-  for (int a = 0; a < cnt[2]; ++a)
-    for (int b = 0; b < cnt[1]; ++b)
-      for (int c = 0; c < cnt[0]; ++c)
-        acc = axpy(acc, wt[0][c] * wt[1][b] * wt[2][a],
-                   Cs[(size_t)idx[0][c] + (size_t)D.c[0] * ((size_t)idx[1][b] + (size_t)D.c[1] * idx[2][a])]);
-  T* Fs = fine + (size_t)s * nf;
-  Fs[i] = add(Fs[i], acc);
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const W wz = a ? w1[2] : w0[2];
+    const T* Cz = Cs + (size_t)(a ? i1[2] : i0[2]) * Pc;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const W wzy = wz * (b ? w1[1] : w0[1]);
+      const T* row = Cz + (b ? i1[1] : i0[1]) * D.c[0];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const W w = wzy * (c ? w1[0] : w0[0]);
+        if (w != W(0)) acc = axpy(acc, w, row[c ? i1[0] : i0[0]]);
+      }
+    }
+  }
+  T* Fs = fine + (size_t)s * nf + (size_t)blockIdx.y * Pf + p;
+  *Fs = add(*Fs, acc);
 }
 
 Dims dims(const LevelGeom& f, const LevelGeom& c) {
@@ -106,7 +135,7 @@ void launch_restrict(const cplx<R>* fine, const LevelGeom& f, cplx<R>* coarse, c
                      const int* act, int na, cudaStream_t st) {
   if (na <= 0) return;
   ProfScope ps(PC_TRANSFER, (double)na * (f.n + c.n) * sizeof(cplx<R>), st);
-  dim3 grd((unsigned)((c.n + 255) / 256), na);
+  dim3 grd((unsigned)((c.K[0] * c.K[1] + 255) / 256), c.K[2], na);
   k_restrict<cplx<R>, R><<<grd, 256, 0, st>>>(fine, coarse, dims(f, c), act, f.n, c.n);
   count_launch();
 }
@@ -116,14 +145,14 @@ void launch_prolong_add(const cplx<R>* coarse, const LevelGeom& c, cplx<R>* fine
                         const int* act, int na, cudaStream_t st) {
   if (na <= 0) return;
   ProfScope ps(PC_TRANSFER, (double)na * (c.n + 2 * f.n) * sizeof(cplx<R>), st);
-  dim3 grd((unsigned)((f.n + 255) / 256), na);
+  dim3 grd((unsigned)((f.K[0] * f.K[1] + 255) / 256), f.K[2], na);
   k_prolong_add<cplx<R>, R><<<grd, 256, 0, st>>>(coarse, fine, dims(f, c), act, f.n, c.n);
   count_launch();
 }
 
 void launch_restrict_model(const double* mf, const LevelGeom& f, double* mc, const LevelGeom& c,
                            cudaStream_t st) {
-  dim3 grd((unsigned)((c.n + 255) / 256), 1);
+  dim3 grd((unsigned)((c.K[0] * c.K[1] + 255) / 256), c.K[2], 1);
   k_restrict<double, double><<<grd, 256, 0, st>>>(mf, mc, dims(f, c), nullptr, f.n, c.n);
   count_launch();
 }
