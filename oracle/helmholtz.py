@@ -16,7 +16,8 @@ Environment for Nonlinear Inverse Problems"):
     T* = w^2 diag(conj u), v = -H^{-H} P_r^T (P_r u - d), grad f = sum Re(T* v);
   * Table derivstuff / Listing pdefunc: the summation over sources and
     frequencies of Re(T(U)^H V), mapped back to the physical grid by the
-    adjoint of the extension (to_phys);
+    adjoint of the extension (to_phys); the linearised data J dm, its adjoint
+    and the Gauss-Newton product J^T J dm;
   * Sec. 4 (Alg. vcycle text): linear-interpolation prolongation and its
     adjoint as restriction; the ML-GMRES V-cycle (GMRES smoothers, coarse
     FGMRES, rediscretised coarse operators) and damped Jacobi as
@@ -456,6 +457,68 @@ def misfit(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, 
     if mask is not None:
         r = r * np.asarray(mask, dtype=np.float64)[..., None]
     return 0.5 * float(np.vdot(r, r).real)
+
+
+# ---------------------------------------------------------------------------
+# Linearised modelling (Appendix A; Table derivstuff): the Jacobian J of the
+# data with respect to the physical m, its adjoint, and the Gauss-Newton
+# Hessian-vector product J^T J
+# ---------------------------------------------------------------------------
+
+def born(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, wavelet=None, mask=None,
+         solver: str = "direct", **solver_kw):
+    """dD = J dm per frequency and source: with u = H^{-1} q the state,
+    H du = -T dm with T dm = w^2 diag(u) E dm (eq. (dU2) with A = I), and
+    dD = P_r du.  Pairs masked out return zeros.  Returns [nfreq, nsrc, nrec]."""
+    mc = extend(g, m_phys)
+    dmc = extend(g, dm_phys).ravel()
+    Qa = np.asarray(Q)
+    nf, ns = len(freqs_hz), Qa.shape[1]
+    dD = np.zeros((nf, ns, len(rec_idx)), dtype=np.complex128)
+    for k in range(nf):
+        om = _omega(freqs_hz[k])
+        w = 1.0 if wavelet is None else wavelet[k]
+        S = make_solver(helmholtz_matrix(g, mc, om), solver, **solver_kw)
+        q = source_fields(g, src_idx, Qa, w)
+        for s in range(ns):
+            if mask is not None and not mask[k][s]:
+                continue
+            u = S.solve(q[s])
+            du = S.solve(-om * om * dmc * u)
+            dD[k, s] = sample_receivers(g, du, rec_idx)
+    return dD
+
+
+def born_adjoint(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, dD, wavelet=None, mask=None,
+                 solver: str = "direct", **solver_kw):
+    """J^T dD for real m: sum over (s, w) of Re(T^* v) with v = -H^{-H} P_r^T dD
+    (eq. (dHadj) with A = I: T^* v = w^2 conj(u) v), mapped by E^T.  Returns
+    g_phys [n_phys] (the gradient formula with the data residual replaced by dD)."""
+    mc = extend(g, m_phys)
+    Qa = np.asarray(Q)
+    dD = np.asarray(dD, dtype=np.complex128)
+    nf, ns = len(freqs_hz), Qa.shape[1]
+    gc = np.zeros(g.size)
+    for k in range(nf):
+        om = _omega(freqs_hz[k])
+        w = 1.0 if wavelet is None else wavelet[k]
+        S = make_solver(helmholtz_matrix(g, mc, om), solver, **solver_kw)
+        q = source_fields(g, src_idx, Qa, w)
+        for s in range(ns):
+            if mask is not None and not mask[k][s]:
+                continue
+            u = S.solve(q[s])
+            v = S.solve_adjoint(-spread_receivers(g, dD[k, s], rec_idx))
+            gc += om * om * np.real(np.conj(u) * v)
+    return extend_adjoint(g, gc)
+
+
+def gauss_newton_hessvec(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, wavelet=None, mask=None,
+                         solver: str = "direct", **solver_kw):
+    """J^T J dm: three PDE solves per (s, w) (state, linearised state, adjoint),
+    Table derivstuff's Gauss-Newton Hessian applied to dm."""
+    dD = born(g, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, wavelet, mask, solver, **solver_kw)
+    return born_adjoint(g, m_phys, freqs_hz, src_idx, Q, rec_idx, dD, wavelet, mask, solver, **solver_kw)
 
 
 # ---------------------------------------------------------------------------

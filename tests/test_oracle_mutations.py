@@ -134,3 +134,81 @@ def test_pin_catches_undamped_sign_flip_in_jacobi(monkeypatch):
     monkeypatch.setattr(O, "jacobi_precond", wrong)
     with pytest.raises(AssertionError):
         TP.test_jacobi_sweeps_converge_to_the_solution_on_a_dominant_diagonal()
+
+
+# ---------------------------------------------------------------------------
+# Linearised-modelling pins (tests/test_oracle_born.py)
+# ---------------------------------------------------------------------------
+
+import inspect  # noqa: E402
+
+import tests.test_oracle_born as TB  # noqa: E402
+
+
+def _born_problem():
+    """The problem of test_oracle_born's fixture, built directly."""
+    return inspect.unwrap(TB.prob)()
+
+
+def test_pin_catches_born_source_sign(monkeypatch):
+    """H du = +T dm (dropped minus sign of eq. (dU2))."""
+    p = _born_problem()
+    real_born = O.born
+    monkeypatch.setattr(O, "born", lambda *a, **k: -real_born(*a, **k))
+    with pytest.raises(AssertionError):
+        TB.test_born_matches_central_differences(p)
+
+
+def test_pin_catches_unconjugated_state_in_adjoint(monkeypatch):
+    """T^* v computed as w^2 u v instead of w^2 conj(u) v."""
+    p = _born_problem()
+
+    def born_adjoint_noconj(g, m_phys, freqs_hz, src_idx, Q, rec_idx, dD, wavelet=None, mask=None, **kw):
+        mc = O.extend(g, m_phys)
+        gc = np.zeros(g.size)
+        for k, fr in enumerate(freqs_hz):
+            om = 2 * np.pi * fr
+            w = 1.0 if wavelet is None else wavelet[k]
+            S = O.DirectSolver(O.helmholtz_matrix(g, mc, om))
+            q = O.source_fields(g, src_idx, np.asarray(Q), w)
+            for s_ in range(np.asarray(Q).shape[1]):
+                u = S.solve(q[s_])
+                v = S.solve_adjoint(-O.spread_receivers(g, np.asarray(dD)[k, s_], rec_idx))
+                gc += om * om * np.real(u * v)
+        return O.extend_adjoint(g, gc)
+
+    monkeypatch.setattr(O, "born_adjoint", born_adjoint_noconj)
+    with pytest.raises(AssertionError):
+        TB.test_adjoint_identity(p)
+
+
+def test_pin_catches_zero_padded_perturbation(monkeypatch):
+    """Extending dm by zeros in the layers (instead of E) changes J dm there."""
+    p = _born_problem()
+    real_extend = O.extend
+
+    def zero_extend(g, x):
+        out = np.zeros(g.shape)
+        n, pm = g.n, g.npml
+        out[pm[2]:pm[2] + n[2], pm[1]:pm[1] + n[1], pm[0]:pm[0] + n[0]] = np.asarray(x).reshape(g.phys_shape)
+        return out
+
+    real_born = O.born
+
+    def born_zero_pad(g, m_phys, *a, **k):
+        # m itself is extended by E; only the perturbation is zero-padded
+        calls = {"n": 0}
+
+        def ext(gg, x):
+            calls["n"] += 1
+            return real_extend(gg, x) if calls["n"] == 1 else zero_extend(gg, x)
+
+        monkeypatch.setattr(O, "extend", ext)
+        try:
+            return real_born(g, m_phys, *a, **k)
+        finally:
+            monkeypatch.setattr(O, "extend", real_extend)
+
+    monkeypatch.setattr(O, "born", born_zero_pad)
+    with pytest.raises(AssertionError):
+        TB.test_born_matches_central_differences(p)
