@@ -66,7 +66,8 @@ typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
 typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGMRES = 2 } helm_precond;
 typedef enum {
   HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
-  HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5, HELM_CALL_PRECOND = 6
+  HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5, HELM_CALL_PRECOND = 6, HELM_CALL_BORN = 7,
+  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9
 } helm_call;
 
 /* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
@@ -205,6 +206,45 @@ int misfit_and_gradient(helm_plan* plan, const double* m_phys, const double* fre
                         void* workspace, size_t ws_bytes, helm_rhs_report* reports,
                         helm_stream_t stream);
 
+/* Linearised modelling (Appendix A eqs. (dU2), (dH), (dHadj) with A = I;
+ * Table derivstuff).  For every selected (k, s) pair the state
+ * u = H(m, w_k)^{-1} q_{k,s} is solved first (sources, wavelet and receivers as
+ * in helm_forward, mask as in misfit_and_gradient; masked-out pairs
+ * contribute nothing), then:
+ *
+ * helm_born:          dD = J dm = P_r du with H du = -w_k^2 (E dm) u
+ *                     (two solves per pair).
+ *     dm_phys  float64 [n_phys];  dD_out complex128 [nfreq][nsrc][nrec]
+ *     (rows of masked-out pairs are zero)
+ * helm_born_adjoint:  g = J^T dD = E^T sum_{k,s} w_k^2 Re(conj(u) v),
+ *                     v = -H^{-H} P_r^T dD_{k,s} (two solves per pair; with
+ *                     dD = P_r u - d it is the misfit gradient).
+ *     dD_in    complex128 [nfreq][nsrc][nrec];  g_out float64 [n_phys]
+ * helm_gn_hessvec:    Hdm = J^T J dm, the Gauss-Newton Hessian applied to dm
+ *                     (three solves per pair).
+ *     dm_phys  float64 [n_phys];  Hdm_out float64 [n_phys]
+ *
+ * J is taken with respect to the physical m (real), so J^T is the adjoint
+ * for the real inner product Re<J dm, dD> = <dm, J^T dD>.  reports (HOST,
+ * [nfreq*nsrc] or NULL) add the iterations of the pair's solves and keep the
+ * worst residual and status.  Workspace: helm_workspace_size with
+ * HELM_CALL_BORN / HELM_CALL_BORN_ADJOINT / HELM_CALL_GN_HESSVEC. */
+int helm_born(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+              const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+              const int32_t* rec_idx, int nrec, const double* dm_phys, const uint8_t* mask,
+              void* dD_out, void* workspace, size_t ws_bytes, helm_rhs_report* reports,
+              helm_stream_t stream);
+int helm_born_adjoint(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                      const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc,
+                      const void* wavelet, const int32_t* rec_idx, int nrec, const void* dD_in,
+                      const uint8_t* mask, double* g_out, void* workspace, size_t ws_bytes,
+                      helm_rhs_report* reports, helm_stream_t stream);
+int helm_gn_hessvec(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                    const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc,
+                    const void* wavelet, const int32_t* rec_idx, int nrec, const double* dm_phys,
+                    const uint8_t* mask, double* Hdm_out, void* workspace, size_t ws_bytes,
+                    helm_rhs_report* reports, helm_stream_t stream);
+
 /* Misfit alone (Table derivcosts: one PDE per source and frequency):
  *   f = sum_{k,s} 1/2 ||P_r u_{k,s} - d_{k,s}||^2,  u = H(m, w_k)^{-1} q_{k,s},
  * over the (k, s) pairs whose mask byte is non-zero (all when mask is NULL).
@@ -286,6 +326,16 @@ int helm_misfit_and_gradient_batch(helm_batch_item* items, int nitems, int nwork
 #define HELM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int helm_apply_noalloc(helm_plan* plan, const double* m_phys, double freq_hz, int adjoint,
                        int precision, const void* x, void* y, int nrhs, helm_stream_t stream);
+
+/* Diagnostic (no counterpart in the paper): checks, on the device of the
+ * current context, how the library reports a bounded device wait that runs
+ * out.  One thread waits -- with the same bounded wait the streamed kernels
+ * use on their bulk copies -- on an mbarrier phase that nothing completes;
+ * after about half a second (2^30 SM cycles) it gives up and the call returns
+ * HELM_E_TIMEOUT, with the CUDA context still usable.  HELM_OK would mean
+ * the wait completed (never expected); HELM_E_CUDA a launch or copy error.
+ * Blocks the host for the duration of the wait. */
+int helm_check_bounded_wait(helm_stream_t stream);
 
 /* Static description of a status code. */
 const char* helm_status_string(int status);

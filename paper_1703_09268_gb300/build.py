@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhelm.so")
 
-SOURCES = ["abi.cu", "solver.cu", "stencil.cu", "krylov.cu", "transfer.cu", "fwi.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["abi.cu", "solver.cu", "stencil.cu", "krylov.cu", "transfer.cu", "fwi.cu", "noalloc.cu", "batch.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

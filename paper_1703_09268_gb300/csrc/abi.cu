@@ -244,7 +244,7 @@ int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys)
 
 int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
   if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
-  if (call < HELM_CALL_APPLY || call > HELM_CALL_PRECOND) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_GN_HESSVEC) return HELM_E_INVAL;
   *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
   return HELM_OK;
 }
@@ -459,6 +459,111 @@ static int mask_list(Ctx& c, const uint8_t* mask, int nrhs, std::vector<int>& to
   for (int i = 0; i < nrhs; ++i)
     if (mh[i]) todo.push_back(i);
   return HELM_OK;
+}
+
+// Per-pair report of several solves: iterations added, the worst residual and status.
+static void merge_reports(std::vector<SlotReport>& acc, const std::vector<SlotReport>& add) {
+  for (size_t a = 0; a < acc.size(); ++a) {
+    acc[a].iters += add[a].iters;
+    acc[a].refine += add[a].refine;
+    acc[a].rel = std::max(acc[a].rel, add[a].rel);
+    acc[a].status = worst(acc[a].status, add[a].status);
+  }
+}
+
+// The linearised calls (Appendix A): kind 0 = J dm, 1 = J^T dD, 2 = J^T J dm.
+static int linearised(int kind, helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
+                      const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                      const int32_t* rec_idx, int nrec, const double* dm_phys, const void* dD_in,
+                      const uint8_t* mask, void* dD_out, double* g_out, void* ws, size_t ws_bytes,
+                      helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1) return HELM_E_INVAL;
+  if ((kind != 1 && !dm_phys) || (kind == 1 && !dD_in) || (kind == 0 && !dD_out) || (kind != 0 && !g_out))
+    return HELM_E_INVAL;
+  const int call = kind == 0 ? HELM_CALL_BORN : kind == 1 ? HELM_CALL_BORN_ADJOINT : HELM_CALL_GN_HESSVEC;
+  Ctx c;
+  if ((st = bind(P, call, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, src_idx, n_srcloc, rec_idx, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  std::vector<int> todo;
+  if ((st = mask_list(c, mask, nrhs, todo)) != HELM_OK) return st;
+  if (reports)
+    for (int i = 0; i < nrhs; ++i) reports[i] = helm_rhs_report{HELM_OK, 0, 0, 0.0};
+  if (kind == 0) cudaMemsetAsync(dD_out, 0, sizeof(double2) * (size_t)nrhs * nrec, c.st);
+  if (kind != 0) cudaMemsetAsync(c.gcomp, 0, sizeof(double) * n, c.st);
+  if (kind != 1) launch_extend(*P, dm_phys, c.dmc, nullptr, c.st);
+  int result = HELM_OK;
+  for (size_t start = 0; start < todo.size(); start += c.B) {
+    const int nb = (int)std::min<size_t>(c.B, todo.size() - start);
+    std::vector<int> g(todo.begin() + start, todo.begin() + start + nb);
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    // state u = H^{-1} q
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, (const double2*)wavelet, c.slot_f,
+                   c.slot_s, nb, c.q, c.err + 1, c.st);
+    std::vector<SlotReport> rep, r2;
+    st = solve_batch(c, 0, c.q, c.u, nb, rep);
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
+    result = worst(result, st);
+    if (kind != 1) {
+      // linearised state du = H^{-1}(-T dm), data dD = P_r du
+      launch_born_source(c.u, c.dmc, c.w2_64, c.slot_f, nb, n, c.q, c.st);
+      st = solve_batch(c, 0, c.q, c.v, nb, r2);
+      if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
+      result = worst(result, st);
+      merge_reports(rep, r2);
+      if (kind == 0)
+        launch_receivers(*P, c.v, rec_idx, nrec, c.slot_g, nb, (double2*)dD_out, nrec, c.st);
+      else
+        launch_receivers(*P, c.v, rec_idx, nrec, c.ident, nb, c.res, nrec, c.st);
+    }
+    if (kind != 0) {
+      // adjoint state v = -H^{-H} P_r^T dD, then g += w^2 Re(conj(u) v)
+      cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+      if (kind == 1)
+        launch_spread(*P, (const double2*)dD_in, nrec, rec_idx, nrec, -1.0, c.slot_g, nb, c.q, c.st);
+      else
+        launch_spread(*P, c.res, nrec, rec_idx, nrec, -1.0, c.ident, nb, c.q, c.st);
+      st = solve_batch(c, 1, c.q, c.v, nb, r2);
+      if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
+      result = worst(result, st);
+      merge_reports(rep, r2);
+      launch_grad_accum(c.u, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    }
+    for (auto& r : rep) result = worst(result, r.status);
+    fill_reports(reports, g, rep);
+  }
+  if (kind != 0) launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  return result;
+}
+
+int helm_born(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,
+              int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
+              const double* dm_phys, const uint8_t* mask, void* dD_out, void* ws, size_t ws_bytes,
+              helm_rhs_report* reports, helm_stream_t stream) {
+  return linearised(0, P, m_phys, freqs_hz, nfreq, src_idx, n_srcloc, Q, nsrc, wavelet, rec_idx, nrec, dm_phys,
+                    nullptr, mask, dD_out, nullptr, ws, ws_bytes, reports, stream);
+}
+
+int helm_born_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,
+                      int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
+                      const void* dD_in, const uint8_t* mask, double* g_out, void* ws, size_t ws_bytes,
+                      helm_rhs_report* reports, helm_stream_t stream) {
+  return linearised(1, P, m_phys, freqs_hz, nfreq, src_idx, n_srcloc, Q, nsrc, wavelet, rec_idx, nrec, nullptr,
+                    dD_in, mask, nullptr, g_out, ws, ws_bytes, reports, stream);
+}
+
+int helm_gn_hessvec(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,
+                    int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
+                    const double* dm_phys, const uint8_t* mask, double* Hdm_out, void* ws, size_t ws_bytes,
+                    helm_rhs_report* reports, helm_stream_t stream) {
+  return linearised(2, P, m_phys, freqs_hz, nfreq, src_idx, n_srcloc, Q, nsrc, wavelet, rec_idx, nrec, dm_phys,
+                    nullptr, mask, nullptr, Hdm_out, ws, ws_bytes, reports, stream);
 }
 
 int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,

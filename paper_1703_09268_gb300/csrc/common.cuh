@@ -223,6 +223,9 @@ void launch_spread(const helm_plan& P, const double2* r, size_t r_stride, const 
                    int nrec, double sign, const int* slots, int nslots, double2* b, cudaStream_t st);
 void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
                        const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st);
+// b_s = -w_f^2 dmc u_s for slots 0..nslots-1 (linearised state right-hand side)
+void launch_born_source(const double2* u, const double* dmc, const double* w2, const int* slot_f, int nslots,
+                        size_t n, double2* b, cudaStream_t st);
 void launch_extend_adjoint(const helm_plan& P, const double* gcomp, double* g_phys, cudaStream_t st);
 void launch_sum_f(const double* f_slot, const int* slots, int nslots, double* f_out, int accumulate,
                   cudaStream_t st);

@@ -241,6 +241,19 @@ __global__ void k_grad_accum(const double2* __restrict__ u, const int* __restric
   gcomp[p] = acc;
 }
 
+// Right-hand side of the linearised state equation (Appendix A, eq. (dU2)
+// with A = I): b = -T dm = -w^2 (E dm) u, per slot.
+__global__ void k_born_source(const double2* __restrict__ u, const double* __restrict__ dmc,
+                              const double* __restrict__ w2, const int* __restrict__ slot_f, size_t n,
+                              double2* __restrict__ b) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int s = blockIdx.y;
+  const double c = -w2[slot_f[s]] * dmc[p];
+  const double2 uu = u[(size_t)s * n + p];
+  b[(size_t)s * n + p] = make_double2(c * uu.x, c * uu.y);
+}
+
 // g_phys = E^T gcomp: each physical node sums the computational nodes copying it.
 __global__ void k_extend_adjoint(GeomArgs g, const double* __restrict__ gc, double* __restrict__ gp) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -370,6 +383,14 @@ void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, con
                        const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st) {
   if (nslots <= 0) return;
   k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n, gcomp);
+  count_launch();
+}
+
+void launch_born_source(const double2* u, const double* dmc, const double* w2, const int* slot_f, int nslots,
+                        size_t n, double2* b, cudaStream_t st) {
+  if (nslots <= 0) return;
+  dim3 grd((unsigned)((n + 255) / 256), nslots);
+  k_born_source<<<grd, 256, 0, st>>>(u, dmc, w2, slot_f, n, b);
   count_launch();
 }
 

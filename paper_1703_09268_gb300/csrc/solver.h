@@ -75,6 +75,7 @@ struct Ctx {
   double2* res = nullptr;  // [B][nrec] receiver residuals
   double* f_slot = nullptr;
   double* gcomp = nullptr;
+  double* dmc = nullptr;   // extended model perturbation E dm (linearised calls)
   // Krylov hierarchies
   Hierarchy<float> h32;
   Hierarchy<double> h64;

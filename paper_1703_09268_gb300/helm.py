@@ -23,6 +23,7 @@ FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
 CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT, CALL_PRECOND = \
     0, 1, 2, 3, 4, 5, 6
+CALL_BORN, CALL_BORN_ADJOINT, CALL_GN_HESSVEC = 7, 8, 9
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
                 "misc", "stencil_c64_coarse", "krylov_c64_coarse", "gram_c64", "update_c64"]
 
@@ -59,8 +60,9 @@ class HelmBatchItem(ctypes.Structure):
 
 EXPORTS = ["helm_default_opts", "helm_misfit_and_gradient_batch", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
            "helm_workspace_size", "helm_apply", "helm_precond_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
-           "helm_misfit", "helm_gradient",
-           "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read"]
+           "helm_misfit", "helm_gradient", "helm_born", "helm_born_adjoint", "helm_gn_hessvec",
+           "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read",
+           "helm_check_bounded_wait"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -83,11 +85,15 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(HelmRhsReport), P]
     lib.misfit_and_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, S,
                                         ctypes.POINTER(HelmRhsReport), P]
+    for name in ("helm_born", "helm_born_adjoint", "helm_gn_hessvec"):
+        getattr(lib, name).argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, S,
+                                       ctypes.POINTER(HelmRhsReport), P]
     lib.helm_misfit.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, P, S,
                                 ctypes.POINTER(HelmRhsReport), P]
     lib.helm_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, P, P, S,
                                   ctypes.POINTER(HelmRhsReport), P]
     lib.helm_misfit_and_gradient_batch.argtypes = [ctypes.POINTER(HelmBatchItem), I, I]
+    lib.helm_check_bounded_wait.argtypes = [P]
     lib.helm_status_string.argtypes = [I]
     lib.helm_status_string.restype = ctypes.c_char_p
     lib.helm_kernel_launch_count.argtypes = []
@@ -275,6 +281,11 @@ def helm_precond_apply(plan: Plan, m_phys: torch.Tensor, freq_hz: float, x: torc
     return z
 
 
+def check_bounded_wait(device="cuda") -> int:
+    """Status of the library's bounded-wait self-check (HELM_E_TIMEOUT expected)."""
+    return int(lib().helm_check_bounded_wait(_stream(torch.device(device))))
+
+
 def _reports(n):
     return (HelmRhsReport * n)()
 
@@ -356,6 +367,57 @@ def misfit_and_gradient(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs
                                      _ptr(d_obs), _ptr(mask), _ptr(f), _ptr(g), ws, nb, rep, _stream(dev))
     _check(code, "misfit_and_gradient", allow_noconv=True)
     return f, g, reports_to_list(rep)
+
+
+def _linearised(name, call, plan, m_phys, freqs_hz, src_idx, Q, rec_idx, vec, wavelet, mask):
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(src_idx, torch.int32, "src_idx")
+    _dev(Q, torch.complex128, "Q")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    if wavelet is not None:
+        _dev(wavelet, torch.complex128, "wavelet")
+    if mask is not None:
+        _dev(mask, torch.uint8, "mask")
+    nfreq = len(np.atleast_1d(freqs_hz))
+    _check_common(plan, m_phys, src_idx, Q, wavelet, nfreq)
+    nsrc, nrec = Q.shape[1], rec_idx.numel()
+    if mask is not None:
+        _need(mask.numel() == nfreq * nsrc, "mask must be [nfreq, nsrc]")
+    dev = m_phys.device
+    if call == CALL_BORN_ADJOINT:
+        _dev(vec, torch.complex128, "dD")
+        _need(tuple(vec.shape) == (nfreq, nsrc, nrec), "dD must be [nfreq, nsrc, nrec]")
+    else:
+        _dev(vec, torch.float64, "dm_phys")
+        _need(vec.numel() == plan.n_phys, f"dm_phys must hold n_phys={plan.n_phys} values")
+    if call == CALL_BORN:
+        out = torch.empty((nfreq, nsrc, nrec), dtype=torch.complex128, device=dev)
+    else:
+        out = torch.empty(plan.n_phys, dtype=torch.float64, device=dev)
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(call, nfreq, nsrc, nrec))
+    code = getattr(lib(), name)(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx), src_idx.numel(),
+                                _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(vec), _ptr(mask), _ptr(out),
+                                ws, nb, rep, _stream(dev))
+    _check(code, name, allow_noconv=True)
+    return out, reports_to_list(rep)
+
+
+def helm_born(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, wavelet=None, mask=None):
+    """dD = J dm [nfreq, nsrc, nrec] complex128 (two solves per pair); returns (dD, reports)."""
+    return _linearised("helm_born", CALL_BORN, plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, wavelet, mask)
+
+
+def helm_born_adjoint(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dD, wavelet=None, mask=None):
+    """g = J^T dD [n_phys] float64 (two solves per pair); returns (g, reports)."""
+    return _linearised("helm_born_adjoint", CALL_BORN_ADJOINT, plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dD,
+                       wavelet, mask)
+
+
+def helm_gn_hessvec(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, wavelet=None, mask=None):
+    """J^T J dm [n_phys] float64 (three solves per pair); returns (Hdm, reports)."""
+    return _linearised("helm_gn_hessvec", CALL_GN_HESSVEC, plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys,
+                       wavelet, mask)
 
 
 def helm_misfit(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, mask=None,
