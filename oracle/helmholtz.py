@@ -521,6 +521,41 @@ def gauss_newton_hessvec(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys
     return born_adjoint(g, m_phys, freqs_hz, src_idx, Q, rec_idx, dD, wavelet, mask, solver, **solver_kw)
 
 
+def hessvec(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, dm_phys, wavelet=None, mask=None,
+            solver: str = "direct", **solver_kw):
+    """Full Hessian of the least-squares misfit applied to dm (Table derivstuff,
+    last row; Appendix A with A = I and phi = 1/2 ||. - d||^2, so the Hessian of
+    phi is the identity).  Four PDE solves per (s, w):
+
+        u   = H^{-1} q,                 du  = -H^{-1} (w^2 (E dm) u)
+        v   = -H^{-H} P_r^T (P_r u - d),
+        dv  = H^{-H} ( -w^2 (E dm) v - P_r^T P_r du )      (DV(m)[dm] of the table)
+        Hdm = E^T sum Re( w^2 conj(du) v + w^2 conj(u) dv ) (DT^*[dm, du] V + T^* DV)
+
+    The sign of the DH^H v term follows from differentiating H^H v = -P_r^T r."""
+    mc = extend(g, m_phys)
+    dmc = extend(g, dm_phys).ravel()
+    Qa = np.asarray(Q)
+    d_obs = np.asarray(d_obs, dtype=np.complex128)
+    nf, ns = len(freqs_hz), Qa.shape[1]
+    gc = np.zeros(g.size)
+    for k in range(nf):
+        om = _omega(freqs_hz[k])
+        w = 1.0 if wavelet is None else wavelet[k]
+        S = make_solver(helmholtz_matrix(g, mc, om), solver, **solver_kw)
+        q = source_fields(g, src_idx, Qa, w)
+        for s in range(ns):
+            if mask is not None and not mask[k][s]:
+                continue
+            u = S.solve(q[s])
+            r = sample_receivers(g, u, rec_idx) - d_obs[k, s]
+            v = S.solve_adjoint(-spread_receivers(g, r, rec_idx))
+            du = S.solve(-om * om * dmc * u)
+            dv = S.solve_adjoint(-om * om * dmc * v - spread_receivers(g, sample_receivers(g, du, rec_idx), rec_idx))
+            gc += om * om * np.real(np.conj(du) * v + np.conj(u) * dv)
+    return extend_adjoint(g, gc)
+
+
 # ---------------------------------------------------------------------------
 # Inter-grid transfers of the V-cycle (Sec. 4): linear interpolation P and
 # restriction R = 2^-dim P^T (full weighting)

@@ -91,3 +91,52 @@ def test_mask_drops_pairs(prob):
     assert np.allclose(J[0, 0], full[0, 0]) and np.allclose(J[1, 1], full[1, 1])
     dD = p["dD"] * mask[..., None]
     assert np.allclose(_JT(p, p["dD"], mask), _JT(p, dD), rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Full Hessian-vector product (Table derivstuff, last row)
+# ---------------------------------------------------------------------------
+
+def _dobs(p, scale=0.2):
+    _, D = O.forward(p["g"], p["m"], p["freqs"], p["src"], p["Q"], p["rec"], p["wav"], want_fields=False)
+    return D + scale * p["dD"]
+
+
+def _H(p, d_obs, dm):
+    return O.hessvec(p["g"], p["m"], p["freqs"], p["src"], p["Q"], p["rec"], d_obs, dm, p["wav"]).ravel()
+
+
+def test_hessvec_matches_central_differences_of_the_gradient(prob):
+    p = prob
+    d_obs = _dobs(p)
+
+    def grad(t):
+        _, g = O.misfit_and_gradient(p["g"], p["m"] + t * p["dm"], p["freqs"], p["src"], p["Q"], p["rec"], d_obs,
+                                     p["wav"])
+        return g.ravel()
+
+    def cd(t):
+        return (grad(t) - grad(-t)) / (2 * t)
+
+    t = 0.5
+    fd = (4 * cd(t / 2) - cd(t)) / 3
+    Hdm = _H(p, d_obs, p["dm"])
+    assert np.linalg.norm(Hdm - fd) / np.linalg.norm(Hdm) < 1e-6
+
+
+def test_hessvec_is_symmetric(prob):
+    """<dm1, H dm2> = <H dm1, dm2> (the paper's Hessian adjoint test, Sec. 5.1)."""
+    p = prob
+    d_obs = _dobs(p)
+    a = p["dm"]
+    b = p["rng"].standard_normal(p["g"].n_phys) * 1e-8
+    Ha, Hb = _H(p, d_obs, a), _H(p, d_obs, b)
+    assert abs(np.dot(a, Hb) - np.dot(Ha, b)) <= 1e-11 * abs(np.dot(a, Hb))
+
+
+def test_hessvec_at_zero_residual_is_gauss_newton(prob):
+    """With d = P_r u(m) the adjoint field vanishes and only J^T J dm remains."""
+    p = prob
+    H0 = _H(p, _dobs(p, 0.0), p["dm"])
+    GN = O.gauss_newton_hessvec(p["g"], p["m"], p["freqs"], p["src"], p["Q"], p["rec"], p["dm"], p["wav"]).ravel()
+    assert np.linalg.norm(H0 - GN) <= 1e-12 * np.linalg.norm(GN)

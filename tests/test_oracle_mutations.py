@@ -212,3 +212,33 @@ def test_pin_catches_zero_padded_perturbation(monkeypatch):
     monkeypatch.setattr(O, "born", born_zero_pad)
     with pytest.raises(AssertionError):
         TB.test_born_matches_central_differences(p)
+
+
+def test_pin_catches_plus_sign_of_dh_adjoint_term(monkeypatch):
+    """dv = H^{-H}(+w^2 dm v - P^T P du) (the other sign) fails the gradient
+    central-difference check."""
+    p = _born_problem()
+
+    def hessvec_plus(g, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, dm_phys, wavelet=None, mask=None, **kw):
+        mc = O.extend(g, m_phys)
+        dmc = O.extend(g, dm_phys).ravel()
+        gc = np.zeros(g.size)
+        Qa = np.asarray(Q)
+        for k, fr in enumerate(freqs_hz):
+            om = 2 * np.pi * fr
+            w = 1.0 if wavelet is None else wavelet[k]
+            S = O.DirectSolver(O.helmholtz_matrix(g, mc, om))
+            q = O.source_fields(g, src_idx, Qa, w)
+            for s_ in range(Qa.shape[1]):
+                u = S.solve(q[s_])
+                r = O.sample_receivers(g, u, rec_idx) - np.asarray(d_obs)[k, s_]
+                v = S.solve_adjoint(-O.spread_receivers(g, r, rec_idx))
+                du = S.solve(-om * om * dmc * u)
+                dv = S.solve_adjoint(om * om * dmc * v
+                                     - O.spread_receivers(g, O.sample_receivers(g, du, rec_idx), rec_idx))
+                gc += om * om * np.real(np.conj(du) * v + np.conj(u) * dv)
+        return O.extend_adjoint(g, gc)
+
+    monkeypatch.setattr(O, "hessvec", hessvec_plus)
+    with pytest.raises(AssertionError):
+        TB.test_hessvec_matches_central_differences_of_the_gradient(p)
