@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "misfit+gradient (src·freq)/s and stencil Gpts/s, % HBM roofline, at ≤1e-8 rel err"
 METRIC_GN = "Gauss-Newton Hessian-vector product J^T J dm (src\u00b7freq)/s (3 PDE solves per pair)"
+METRIC_HESS = "full Hessian-vector product of the misfit (src\u00b7freq)/s (4 PDE solves per pair)"
 UNIT = "(src·freq)/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
@@ -56,8 +57,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--workers", type=int, default=4, help="batch mode: models in flight together")
-    p.add_argument("--op", default="misfit_grad", choices=["misfit_grad", "gn"],
-                   help="step mode: misfit + gradient, or the Gauss-Newton Hessian-vector product J^T J dm")
+    p.add_argument("--op", default="misfit_grad", choices=["misfit_grad", "gn", "hess"],
+                   help="step mode: misfit + gradient, the Gauss-Newton product J^T J dm, or the full Hessian product")
     p.add_argument("--mode", default="step", choices=["step", "apply", "batch"],
                    help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
                         "workload's 16 complex64 fields)")
@@ -347,15 +348,19 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    gn = args.op == "gn"
-    # a seeded model perturbation for the Gauss-Newton product (input, resident)
-    dmv = T(np.random.default_rng(7).standard_normal(wl.m0.size) * 1e-9, torch.float64) if gn else None
+    gn, hess = args.op == "gn", args.op == "hess"
+    # a seeded model perturbation for the Hessian products (input, resident)
+    dmv = T(np.random.default_rng(7).standard_normal(wl.m0.size) * 1e-9, torch.float64) if gn or hess else None
 
     def step(p=plan, reduce=True, m=None, s_=None, q_=None, r_=None, d_=None, dm_=None):
         m, s_, q_, r_ = (m0 if m is None else m), (src if s_ is None else s_), (Q if q_ is None else q_), \
             (rec if r_ is None else r_)
-        if gn:
-            h, rep = helm.helm_gn_hessvec(p, m, wl.freqs_hz, s_, q_, r_, dmv if dm_ is None else dm_)
+        if gn or hess:
+            dmx = dmv if dm_ is None else dm_
+            if gn:
+                h, rep = helm.helm_gn_hessvec(p, m, wl.freqs_hz, s_, q_, r_, dmx)
+            else:
+                h, rep = helm.helm_hessvec(p, m, wl.freqs_hz, s_, q_, r_, d_obs if d_ is None else d_, dmx)
             if world > 1 and reduce:
                 dist.all_reduce(h)
             return None, h, rep
@@ -425,7 +430,8 @@ def main():
                    frac=round(st["bytes"] / (st["ms"] / 1e3) / 1e9 / hbm, 3),
                    launches=st["launches"], avg_launch_us=round(1e3 * st["ms"] / max(st["launches"], 1), 2))
 
-    out = dict(metric=METRIC_GN if gn else METRIC, value=round(value, 3), unit=UNIT, n_gpus=world, steps=args.steps,
+    out = dict(metric=METRIC_GN if gn else METRIC_HESS if hess else METRIC, value=round(value, 3), unit=UNIT,
+               n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms_max, 3), higher_is_better=True, scaling="weak",
                vs_baseline=None, dtype="c64 inner / f64 refine" if args.precision == "mixed" else "f64",
                data="synthetic (seeded layered model, observed data modelled in FP64)",
@@ -434,14 +440,15 @@ def main():
                            levels=levels, k_inner=kin, smoother=args.smoother, tol=args.tol,
                            tol_inner=args.tol_inner, reorth=args.reorth, l2="flushed between timed steps (256 MB)",
                            parallelism=f"dp{world} over sources, f and g all-reduced" if world > 1 else "1 GPU",
-                           op="J^T J dm (3 solves per pair)" if gn else "misfit + gradient (2 solves per pair)"),
+                           op="J^T J dm (3 solves per pair)" if gn else
+                           "full Hessian times dm (4 solves per pair)" if hess else "misfit + gradient (2 solves per pair)"),
                roofline=roofline, stencil=stencil, gpu_launches=int(launches),
                solver=dict(outer_iters_per_pair=float(np.mean(iters)), refinements_per_pair=float(np.mean(refs)),
                            max_rel_resid=float(max(r["rel_resid"] for r in rep))),
                clocks=clk)
     if rank == 0:
         # accuracy against the FP64 GPU path (itself checked against the oracle in tests)
-        if args.precision == "mixed" and gn:
+        if args.precision == "mixed" and (gn or hess):
             _, h64, _ = step(p=p64, reduce=False)
             _, h1, _ = step(reduce=False)
             out["accuracy"] = dict(reference="FP64 GPU path, FGMRES+ML-GMRES to rel. residual 1e-13",
@@ -453,7 +460,7 @@ def main():
                 reference="FP64 GPU path, FGMRES+ML-GMRES to rel. residual 1e-13",
                 f_rel_err=float(abs(f1.item() - f64.item()) / abs(f64.item())),
                 g_rel_err=float((g1 - g64).norm().item() / g64.norm().item()))
-        if not args.no_fp64_baseline and not gn:
+        if not args.no_fp64_baseline and not (gn or hess):
             pb = helm.Plan(grid, helm.default_opts(precision=helm.FP64, precond=prec, k_inner=kin, tol=args.tol,
                                                    max_cycles=400, max_batch=1), device=dev)
             helm.misfit_and_gradient(pb, m0, wl.freqs_hz, src, Q, rec, d_obs)
@@ -469,7 +476,8 @@ def main():
                                           what="FP64 FGMRES+same preconditioner, one right-hand side at a time")
         # end to end through the public API with host buffers
         hm = torch.as_tensor(wl.m0.ravel(), dtype=torch.float64).pin_memory()
-        hd = (dmv if gn else d_obs).cpu().pin_memory()
+        hd = d_obs.cpu().pin_memory()
+        hdm = dmv.cpu().pin_memory() if dmv is not None else None
         hs, hq, hr = src.cpu().pin_memory(), Q.cpu().pin_memory(), rec.cpu().pin_memory()
         e2e_t = []
         for i in range(args.steps + 1):
@@ -478,14 +486,16 @@ def main():
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             dm, dd = hm.to(dev, non_blocking=True), hd.to(dev, non_blocking=True)
+            ddm = hdm.to(dev, non_blocking=True) if hdm is not None else None
             ds, dq, dr = hs.to(dev, non_blocking=True), hq.to(dev, non_blocking=True), hr.to(dev, non_blocking=True)
-            f, g, _ = step(reduce=False, m=dm, s_=ds, q_=dq, r_=dr, d_=dd, dm_=dd)
+            f, g, _ = step(reduce=False, m=dm, s_=ds, q_=dq, r_=dr, d_=dd, dm_=ddm)
             fh, gh = (f.cpu() if f is not None else torch.zeros(0)), g.cpu()
             e1.record(stream)
             torch.cuda.synchronize()
             if i > 0:
                 e2e_t.append(e0.elapsed_time(e1))
-        h2d = sum(t.numel() * t.element_size() for t in (hm, hd, hs, hq, hr))
+        h2d = sum(t.numel() * t.element_size() for t in (hm, hd, hs, hq, hr)) + \
+            (hdm.numel() * hdm.element_size() if hdm is not None else 0)
         d2h = fh.numel() * 8 + gh.numel() * 8
         out["e2e"] = dict(value=round(units / (np.mean(e2e_t) / 1e3), 3), unit=UNIT, h2d_bytes_per_step=int(h2d),
                           d2h_bytes_per_step=int(d2h))

@@ -67,7 +67,7 @@ typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGM
 typedef enum {
   HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
   HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5, HELM_CALL_PRECOND = 6, HELM_CALL_BORN = 7,
-  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9
+  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9, HELM_CALL_HESSVEC = 10
 } helm_call;
 
 /* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
@@ -244,6 +244,21 @@ int helm_gn_hessvec(helm_plan* plan, const double* m_phys, const double* freqs_h
                     const void* wavelet, const int32_t* rec_idx, int nrec, const double* dm_phys,
                     const uint8_t* mask, double* Hdm_out, void* workspace, size_t ws_bytes,
                     helm_rhs_report* reports, helm_stream_t stream);
+
+/* Full Hessian of the misfit applied to dm (Table derivstuff, last row;
+ * Appendix A with A = I and the least-squares phi, whose Hessian is the
+ * identity).  Four solves per selected (k, s) pair:
+ *   u  = H^{-1} q,   v = -H^{-H} P_r^T (P_r u - d),   du = -H^{-1} w^2 (E dm) u,
+ *   dv = H^{-H} ( -w^2 (E dm) v - P_r^T P_r du ),
+ *   Hdm = E^T sum_{k,s} w_k^2 Re( conj(du) v + conj(u) dv ).
+ * Arguments as helm_gn_hessvec plus d_obs (complex128 [nfreq][nsrc][nrec], as
+ * misfit_and_gradient).  At zero data residual it equals helm_gn_hessvec.
+ * Workspace: helm_workspace_size with HELM_CALL_HESSVEC. */
+int helm_hessvec(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                 const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                 const int32_t* rec_idx, int nrec, const void* d_obs, const double* dm_phys,
+                 const uint8_t* mask, double* Hdm_out, void* workspace, size_t ws_bytes,
+                 helm_rhs_report* reports, helm_stream_t stream);
 
 /* Misfit alone (Table derivcosts: one PDE per source and frequency):
  *   f = sum_{k,s} 1/2 ||P_r u_{k,s} - d_{k,s}||^2,  u = H(m, w_k)^{-1} q_{k,s},

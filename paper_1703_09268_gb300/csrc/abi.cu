@@ -244,7 +244,7 @@ int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys)
 
 int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
   if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
-  if (call < HELM_CALL_APPLY || call > HELM_CALL_GN_HESSVEC) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_HESSVEC) return HELM_E_INVAL;
   *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
   return HELM_OK;
 }
@@ -471,7 +471,8 @@ static void merge_reports(std::vector<SlotReport>& acc, const std::vector<SlotRe
   }
 }
 
-// The linearised calls (Appendix A): kind 0 = J dm, 1 = J^T dD, 2 = J^T J dm.
+// The linearised calls (Appendix A): kind 0 = J dm, 1 = J^T dD, 2 = J^T J dm,
+// 3 = full Hessian of the misfit times dm (dD_in then holds d_obs).
 static int linearised(int kind, helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
                       const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
                       const int32_t* rec_idx, int nrec, const double* dm_phys, const void* dD_in,
@@ -480,9 +481,13 @@ static int linearised(int kind, helm_plan* P, const double* m_phys, const double
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1) return HELM_E_INVAL;
-  if ((kind != 1 && !dm_phys) || (kind == 1 && !dD_in) || (kind == 0 && !dD_out) || (kind != 0 && !g_out))
+  if ((kind != 1 && !dm_phys) || ((kind == 1 || kind == 3) && !dD_in) || (kind == 0 && !dD_out) ||
+      (kind != 0 && !g_out))
     return HELM_E_INVAL;
-  const int call = kind == 0 ? HELM_CALL_BORN : kind == 1 ? HELM_CALL_BORN_ADJOINT : HELM_CALL_GN_HESSVEC;
+  const int call = kind == 0   ? HELM_CALL_BORN
+                   : kind == 1 ? HELM_CALL_BORN_ADJOINT
+                   : kind == 2 ? HELM_CALL_GN_HESSVEC
+                               : HELM_CALL_HESSVEC;
   Ctx c;
   if ((st = bind(P, call, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
   if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
@@ -509,6 +514,34 @@ static int linearised(int kind, helm_plan* P, const double* m_phys, const double
     st = solve_batch(c, 0, c.q, c.u, nb, rep);
     if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
+    if (kind == 3) {
+      auto solve = [&](int dir, double2* out) {
+        st = solve_batch(c, dir, c.q, out, nb, r2);
+        if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return false;
+        result = worst(result, st);
+        merge_reports(rep, r2);
+        return true;
+      };
+      // adjoint state v = -H^{-H} P_r^T (P_r u - d)
+      launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)dD_in, c.slot_f, c.slot_s, nsrc, c.ident, nb,
+                             c.res, c.f_slot, c.st);
+      cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+      launch_spread(*P, c.res, nrec, rec_idx, nrec, -1.0, c.ident, nb, c.q, c.st);
+      if (!solve(1, c.v)) return st;
+      // linearised state du = -H^{-1} w^2 (E dm) u, then the DT^*[dm, du] v term
+      launch_born_source(c.u, c.dmc, c.w2_64, c.slot_f, nb, n, c.q, c.st);
+      if (!solve(0, c.du)) return st;
+      launch_grad_accum(c.du, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+      // dv = H^{-H}(-w^2 (E dm) v - P_r^T P_r du), then the T^* dv term
+      launch_born_source(c.v, c.dmc, c.w2_64, c.slot_f, nb, n, c.q, c.st);
+      launch_receivers(*P, c.du, rec_idx, nrec, c.ident, nb, c.res, nrec, c.st);
+      launch_spread(*P, c.res, nrec, rec_idx, nrec, -1.0, c.ident, nb, c.q, c.st);
+      if (!solve(1, c.du)) return st;
+      launch_grad_accum(c.u, nullptr, c.du, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+      for (auto& r : rep) result = worst(result, r.status);
+      fill_reports(reports, g, rep);
+      continue;
+    }
     if (kind != 1) {
       // linearised state du = H^{-1}(-T dm), data dD = P_r du
       launch_born_source(c.u, c.dmc, c.w2_64, c.slot_f, nb, n, c.q, c.st);
@@ -556,6 +589,14 @@ int helm_born_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz
                       helm_rhs_report* reports, helm_stream_t stream) {
   return linearised(1, P, m_phys, freqs_hz, nfreq, src_idx, n_srcloc, Q, nsrc, wavelet, rec_idx, nrec, nullptr,
                     dD_in, mask, nullptr, g_out, ws, ws_bytes, reports, stream);
+}
+
+int helm_hessvec(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,
+                 int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
+                 const void* d_obs, const double* dm_phys, const uint8_t* mask, double* Hdm_out, void* ws,
+                 size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  return linearised(3, P, m_phys, freqs_hz, nfreq, src_idx, n_srcloc, Q, nsrc, wavelet, rec_idx, nrec, dm_phys,
+                    d_obs, mask, nullptr, Hdm_out, ws, ws_bytes, reports, stream);
 }
 
 int helm_gn_hessvec(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,

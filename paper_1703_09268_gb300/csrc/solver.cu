@@ -134,7 +134,8 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   const size_t n0 = P.lev[0].n;
   C.q = bp.take<double2>((size_t)B * n0);
   C.u = bp.take<double2>((size_t)B * n0);
-  const bool born = call == HELM_CALL_BORN || call == HELM_CALL_BORN_ADJOINT || call == HELM_CALL_GN_HESSVEC;
+  const bool born = call == HELM_CALL_BORN || call == HELM_CALL_BORN_ADJOINT || call == HELM_CALL_GN_HESSVEC ||
+                    call == HELM_CALL_HESSVEC;
   if (call == HELM_CALL_ADJOINT || call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT || born)
     C.v = bp.take<double2>((size_t)B * n0);
   C.nrm = bp.take<double>(B);
@@ -147,15 +148,17 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   } else {
     layout_hierarchy<double>(bp, P, C.h64, B);
   }
-  if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_MISFIT) {
+  if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_MISFIT || call == HELM_CALL_HESSVEC) {
     C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
     C.f_slot = bp.take<double>(B);
   }
+  if (call == HELM_CALL_HESSVEC) C.du = bp.take<double2>((size_t)B * n0);
   if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT || call == HELM_CALL_BORN_ADJOINT ||
-      call == HELM_CALL_GN_HESSVEC)
+      call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC)
     C.gcomp = bp.take<double>(n0);
   if (call == HELM_CALL_GN_HESSVEC) C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
-  if (call == HELM_CALL_BORN || call == HELM_CALL_GN_HESSVEC) C.dmc = bp.take<double>(n0);
+  if (call == HELM_CALL_BORN || call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC)
+    C.dmc = bp.take<double>(n0);
   return bp.off;
 }
 

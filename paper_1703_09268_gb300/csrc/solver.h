@@ -76,6 +76,7 @@ struct Ctx {
   double* f_slot = nullptr;
   double* gcomp = nullptr;
   double* dmc = nullptr;   // extended model perturbation E dm (linearised calls)
+  double2* du = nullptr;   // linearised state / adjoint (full Hessian product)
   // Krylov hierarchies
   Hierarchy<float> h32;
   Hierarchy<double> h64;

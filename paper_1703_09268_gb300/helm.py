@@ -23,7 +23,7 @@ FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
 CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT, CALL_PRECOND = \
     0, 1, 2, 3, 4, 5, 6
-CALL_BORN, CALL_BORN_ADJOINT, CALL_GN_HESSVEC = 7, 8, 9
+CALL_BORN, CALL_BORN_ADJOINT, CALL_GN_HESSVEC, CALL_HESSVEC = 7, 8, 9, 10
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
                 "misc", "stencil_c64_coarse", "krylov_c64_coarse", "gram_c64", "update_c64"]
 
@@ -60,7 +60,7 @@ class HelmBatchItem(ctypes.Structure):
 
 EXPORTS = ["helm_default_opts", "helm_misfit_and_gradient_batch", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
            "helm_workspace_size", "helm_apply", "helm_precond_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
-           "helm_misfit", "helm_gradient", "helm_born", "helm_born_adjoint", "helm_gn_hessvec",
+           "helm_misfit", "helm_gradient", "helm_born", "helm_born_adjoint", "helm_gn_hessvec", "helm_hessvec",
            "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read",
            "helm_check_bounded_wait"]
 
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     for name in ("helm_born", "helm_born_adjoint", "helm_gn_hessvec"):
         getattr(lib, name).argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, S,
                                        ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_hessvec.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, S,
+                                 ctypes.POINTER(HelmRhsReport), P]
     lib.helm_misfit.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, P, S,
                                 ctypes.POINTER(HelmRhsReport), P]
     lib.helm_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, P, P, S,
@@ -418,6 +420,37 @@ def helm_gn_hessvec(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys, 
     """J^T J dm [n_phys] float64 (three solves per pair); returns (Hdm, reports)."""
     return _linearised("helm_gn_hessvec", CALL_GN_HESSVEC, plan, m_phys, freqs_hz, src_idx, Q, rec_idx, dm_phys,
                        wavelet, mask)
+
+
+def helm_hessvec(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, dm_phys, wavelet=None, mask=None):
+    """Full Hessian of the misfit times dm, [n_phys] float64 (four solves per pair);
+    returns (Hdm, reports)."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(src_idx, torch.int32, "src_idx")
+    _dev(Q, torch.complex128, "Q")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    _dev(d_obs, torch.complex128, "d_obs")
+    _dev(dm_phys, torch.float64, "dm_phys")
+    if wavelet is not None:
+        _dev(wavelet, torch.complex128, "wavelet")
+    if mask is not None:
+        _dev(mask, torch.uint8, "mask")
+    nfreq = len(np.atleast_1d(freqs_hz))
+    _check_common(plan, m_phys, src_idx, Q, wavelet, nfreq)
+    nsrc, nrec = Q.shape[1], rec_idx.numel()
+    _need(tuple(d_obs.shape) == (nfreq, nsrc, nrec), "d_obs must be [nfreq, nsrc, nrec]")
+    _need(dm_phys.numel() == plan.n_phys, f"dm_phys must hold n_phys={plan.n_phys} values")
+    if mask is not None:
+        _need(mask.numel() == nfreq * nsrc, "mask must be [nfreq, nsrc]")
+    dev = m_phys.device
+    out = torch.empty(plan.n_phys, dtype=torch.float64, device=dev)
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_HESSVEC, nfreq, nsrc, nrec))
+    code = lib().helm_hessvec(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx), src_idx.numel(), _ptr(Q),
+                              nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(d_obs), _ptr(dm_phys), _ptr(mask),
+                              _ptr(out), ws, nb, rep, _stream(dev))
+    _check(code, "helm_hessvec", allow_noconv=True)
+    return out, reports_to_list(rep)
 
 
 def helm_misfit(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, mask=None,

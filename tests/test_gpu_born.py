@@ -120,3 +120,19 @@ def test_born_2d_workload(helm):
         GN, rep = helm.helm_gn_hessvec(plan, *args, T(dm, torch.float64))
         assert rel(GN.cpu().numpy(), ref) <= tol
         assert all(r["status"] == 0 for r in rep)
+
+
+@pytest.mark.parametrize("name,extra", [("fp64", {}), ("mixed", {"max_batch": 3})])
+def test_full_hessvec_3d(helm, p3d, name, extra):
+    p = p3d
+    rng = np.random.default_rng(44)
+    _, D = O.forward(p["g"], p["m"], p["freqs"], p["src"], p["Q"], p["rec"], p["wav"], want_fields=False)
+    d_obs = D + 0.2 * (rng.standard_normal(D.shape) + 1j * rng.standard_normal(D.shape))
+    ref = O.hessvec(p["g"], p["m"], p["freqs"], p["src"], p["Q"], p["rec"], d_obs, p["dm"], p["wav"],
+                    p["mask"]).ravel()
+    plan = _plan(helm, p, name, **extra)
+    tol = 1e-10 if name == "fp64" else 1e-8
+    Hdm, rep = helm.helm_hessvec(plan, *_args(p), T(d_obs, torch.complex128), T(p["dm"], torch.float64),
+                                 wavelet=T(p["wav"], torch.complex128), mask=T(p["mask"], torch.uint8))
+    assert rel(Hdm.cpu().numpy(), ref) <= tol
+    assert rep[2]["iters"] == 0 and all(r["status"] == 0 for r in rep)
