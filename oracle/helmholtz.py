@@ -557,6 +557,73 @@ def hessvec(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, dm_phys, wave
 
 
 # ---------------------------------------------------------------------------
+# 2.5D modelling (Sec. 3, "2.5D"): a y-invariant model, a Fourier transform in
+# y, one 2D problem per wavenumber k_y with the shift -k_y^2, and a quadrature
+# sum over k_y
+# ---------------------------------------------------------------------------
+
+def gauss_legendre_ky(k_max: float, nk: int, dy: float = 0.0):
+    """Nodes k_i on [0, k_max] and weights c_i = w_i cos(k_i dy) / pi of the
+    quadrature u(x, y_s + dy, z) = (1/pi) int_0^k_max u~_k(x, z) cos(k dy) dk
+    (Gauss-Legendre, mapped from [-1, 1])."""
+    t, w = np.polynomial.legendre.leggauss(nk)
+    k = 0.5 * k_max * (t + 1.0)
+    c = 0.5 * k_max * w * np.cos(k * dy) / np.pi
+    return k, c
+
+
+def helmholtz_matrix_25d(g: Grid, m_comp: np.ndarray, omega: float, ky: float) -> sp.csr_matrix:
+    """H(k_y) = H(m, omega) - k_y^2 I on a 2D grid (the y derivative becomes -k_y^2)."""
+    assert g.dim == 2
+    H = helmholtz_matrix(g, m_comp, omega)
+    return sp.csr_matrix(H - ky * ky * sp.identity(g.size, dtype=np.complex128, format="csr"))
+
+
+def forward_25d(g: Grid, m_phys, freqs_hz, ky, ck, src_idx, Q, rec_idx, wavelet=None):
+    """2.5D data D[k, s] = sum_i c_i P_r u~_{k_i}, H(k_i) u~ = q (2D point sources,
+    1/h^2 at the node).  Returns (D [nfreq, nsrc, nrec], U [nfreq, nsrc, nk, size])."""
+    mc = extend(g, m_phys)
+    Qa = np.asarray(Q)
+    nf, ns, nk = len(freqs_hz), Qa.shape[1], len(ky)
+    D = np.zeros((nf, ns, len(rec_idx)), dtype=np.complex128)
+    U = np.zeros((nf, ns, nk, g.size), dtype=np.complex128)
+    for k, fr in enumerate(freqs_hz):
+        w = 1.0 if wavelet is None else wavelet[k]
+        q = source_fields(g, src_idx, Qa, w)
+        for i in range(nk):
+            S = DirectSolver(helmholtz_matrix_25d(g, mc, _omega(fr), ky[i]))
+            for s in range(ns):
+                U[k, s, i] = S.solve(q[s])
+                D[k, s] += ck[i] * sample_receivers(g, U[k, s, i], rec_idx)
+    return D, U
+
+
+def misfit_and_gradient_25d(g: Grid, m_phys, freqs_hz, ky, ck, src_idx, Q, rec_idx, d_obs, wavelet=None):
+    """f = sum_{k,s} 1/2 || sum_i c_i P_r u~_i - d ||^2 and its gradient: with the
+    residual r shared by the k_y terms, v_i = -H(k_i)^{-H} P_r^T (c_i r) and
+    g = E^T sum w^2 Re(conj(u~_i) v_i) (the sum structure the section notes for
+    derivatives).  Returns (f, g_phys)."""
+    mc = extend(g, m_phys)
+    d_obs = np.asarray(d_obs, dtype=np.complex128)
+    D, U = forward_25d(g, m_phys, freqs_hz, ky, ck, src_idx, Q, rec_idx, wavelet)
+    f = 0.0
+    gc = np.zeros(g.size)
+    for k, fr in enumerate(freqs_hz):
+        om = _omega(fr)
+        for i in range(len(ky)):
+            S = DirectSolver(helmholtz_matrix_25d(g, mc, om, ky[i]))
+            for s in range(U.shape[1]):
+                r = D[k, s] - d_obs[k, s]
+                v = S.solve_adjoint(-ck[i] * spread_receivers(g, r, rec_idx))
+                gc += om * om * np.real(np.conj(U[k, s, i]) * v)
+    for k in range(len(freqs_hz)):
+        for s in range(D.shape[1]):
+            r = D[k, s] - d_obs[k, s]
+            f += 0.5 * float(np.vdot(r, r).real)
+    return f, extend_adjoint(g, gc)
+
+
+# ---------------------------------------------------------------------------
 # Inter-grid transfers of the V-cycle (Sec. 4): linear interpolation P and
 # restriction R = 2^-dim P^T (full weighting)
 # ---------------------------------------------------------------------------

@@ -242,3 +242,37 @@ def test_pin_catches_plus_sign_of_dh_adjoint_term(monkeypatch):
     monkeypatch.setattr(O, "hessvec", hessvec_plus)
     with pytest.raises(AssertionError):
         TB.test_hessvec_matches_central_differences_of_the_gradient(p)
+
+
+# ---------------------------------------------------------------------------
+# 2.5D pins (tests/test_oracle_25d.py)
+# ---------------------------------------------------------------------------
+
+import tests.test_oracle_25d as T25  # noqa: E402
+
+
+def test_pin_catches_wrong_sign_of_ky_shift(monkeypatch):
+    """H(k_y) = H + k_y^2 I (the y derivative's sign flipped)."""
+    real = O.helmholtz_matrix
+    import scipy.sparse as sp_
+
+    def plus(g, m_comp, omega, ky):
+        return sp_.csr_matrix(real(g, m_comp, omega) + ky * ky * sp_.identity(g.size, dtype=np.complex128))
+
+    monkeypatch.setattr(O, "helmholtz_matrix_25d", plus)
+    with pytest.raises(AssertionError):
+        T25.test_25d_sum_reproduces_the_3d_greens_function()
+
+
+def test_pin_catches_unweighted_adjoint_source(monkeypatch):
+    """v_i = -H_i^{-H} P^T r without the quadrature weight c_i."""
+    real = O.misfit_and_gradient_25d
+
+    def unweighted(g, m_phys, freqs_hz, ky, ck, *a, **k):
+        f, _ = real(g, m_phys, freqs_hz, ky, ck, *a, **k)
+        _, gr = real(g, m_phys, freqs_hz, ky, np.ones_like(ck), *a, **k)
+        return f, gr
+
+    monkeypatch.setattr(O, "misfit_and_gradient_25d", unweighted)
+    with pytest.raises(AssertionError):
+        T25.test_25d_gradient_matches_central_differences()
