@@ -67,7 +67,7 @@ typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGM
 typedef enum {
   HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
   HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5, HELM_CALL_PRECOND = 6, HELM_CALL_BORN = 7,
-  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9, HELM_CALL_HESSVEC = 10
+  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9, HELM_CALL_HESSVEC = 10, HELM_CALL_MISFIT_GRAD_25D = 11
 } helm_call;
 
 /* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
@@ -259,6 +259,29 @@ int helm_hessvec(helm_plan* plan, const double* m_phys, const double* freqs_hz, 
                  const int32_t* rec_idx, int nrec, const void* d_obs, const double* dm_phys,
                  const uint8_t* mask, double* Hdm_out, void* workspace, size_t ws_bytes,
                  helm_rhs_report* reports, helm_stream_t stream);
+
+/* 2.5D misfit and gradient (Sec. 3, 2.5D): a model invariant in y on a 2D
+ * plan (dim = 2, the grid is (x, z)); the y-Fourier transform turns each
+ * frequency into 2D problems H(k_i) u~_i = q with H(k) = H(m, w) - k^2 I (no
+ * layer in y), and the data are the quadrature sum
+ *   D_{k,s} = sum_i ck[i] P_r u~_{k,s,i},
+ * with ck[i] = (quadrature weight) cos(k_i dy) / pi supplied by the caller
+ * (e.g. Gauss-Legendre on [0, p w / v_min], dy = receiver y - source y).
+ *   f = sum_{k,s} 1/2 ||D_{k,s} - d_{k,s}||^2,
+ *   g = E^T sum_{k,s,i} w_k^2 Re(conj(u~_i) v_i),  v_i = -H(k_i)^{-H} P_r^T (ck[i] r_{k,s}).
+ *   ky, ck   HOST float64 [nk] (wavenumbers in rad/m, weights)
+ *   d_obs    complex128 [nfreq][nsrc][nrec]; wavelet as helm_forward
+ *   f_out    float64 [1]; g_out float64 [n_phys] of the 2D plan
+ *   reports  HOST [nfreq][nsrc][nk] or NULL
+ * The nk solves of one (frequency, source) run in the same batch, so
+ * max_batch must be 0 or at least nk.  Workspace: helm_workspace_size with
+ * HELM_CALL_MISFIT_GRAD_25D and nfreq*nk in place of nfreq. */
+int helm_misfit_and_gradient_25d(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                                 const double* ky, const double* ck, int nk, const int32_t* src_idx,
+                                 int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                                 const int32_t* rec_idx, int nrec, const void* d_obs, double* f_out,
+                                 double* g_out, void* workspace, size_t ws_bytes, helm_rhs_report* reports,
+                                 helm_stream_t stream);
 
 /* Misfit alone (Table derivcosts: one PDE per source and frequency):
  *   f = sum_{k,s} 1/2 ||P_r u_{k,s} - d_{k,s}||^2,  u = H(m, w_k)^{-1} q_{k,s},

@@ -244,7 +244,7 @@ int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys)
 
 int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
   if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
-  if (call < HELM_CALL_APPLY || call > HELM_CALL_HESSVEC) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_MISFIT_GRAD_25D) return HELM_E_INVAL;
   *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
   return HELM_OK;
 }
@@ -589,6 +589,85 @@ int helm_born_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz
                       helm_rhs_report* reports, helm_stream_t stream) {
   return linearised(1, P, m_phys, freqs_hz, nfreq, src_idx, n_srcloc, Q, nsrc, wavelet, rec_idx, nrec, nullptr,
                     dD_in, mask, nullptr, g_out, ws, ws_bytes, reports, stream);
+}
+
+int helm_misfit_and_gradient_25d(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
+                                 const double* ky, const double* ck, int nk, const int32_t* src_idx, int n_srcloc,
+                                 const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
+                                 const void* d_obs, double* f_out, double* g_out, void* ws, size_t ws_bytes,
+                                 helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (P->g.dim != 2 || !ky || !ck || nk < 1 || !src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs ||
+      !f_out || !g_out)
+    return HELM_E_INVAL;
+  for (int i = 0; i < nk; ++i)
+    if (!std::isfinite(ky[i]) || !std::isfinite(ck[i])) return HELM_E_INVAL;
+  // virtual frequencies v = j*nk + i: (w_j, k_i)
+  const int nv = nfreq * nk;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_MISFIT_GRAD_25D, nv, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  const int gmax = c.B / nk;  // whole groups of nk slots per batch
+  if (gmax < 1) return HELM_E_INVAL;
+  std::vector<double> fv(nv), sv(nv), cv(nv);
+  for (int j = 0; j < nfreq; ++j)
+    for (int i = 0; i < nk; ++i) {
+      fv[j * nk + i] = freqs_hz[j];
+      sv[j * nk + i] = ky[i] * ky[i];
+      cv[j * nk + i] = ck[i];
+    }
+  cudaMemcpyAsync(c.shift, sv.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, c.st);
+  cudaMemcpyAsync(c.ck, cv.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, c.st);
+  if (wavelet)
+    for (int v = 0; v < nv; ++v)
+      cudaMemcpyAsync(c.wav + v, (const double2*)wavelet + v / nk, sizeof(double2), cudaMemcpyDeviceToDevice, c.st);
+  if ((st = setup_operator(c, m_phys, fv.data())) != HELM_OK) return st;
+  if ((st = check_indices(c, src_idx, n_srcloc, rec_idx, nrec)) != HELM_OK) return st;
+  const size_t n = P->lev[0].n;
+  if (reports)
+    for (int i = 0; i < nv * nsrc; ++i) reports[i] = helm_rhs_report{HELM_OK, 0, 0, 0.0};
+  cudaMemsetAsync(c.gcomp, 0, sizeof(double) * n, c.st);
+  cudaMemsetAsync(f_out, 0, sizeof(double), c.st);
+  const int ngroups_all = nfreq * nsrc;
+  int result = HELM_OK;
+  for (int g0 = 0; g0 < ngroups_all; g0 += gmax) {
+    const int ng = std::min(gmax, ngroups_all - g0);
+    const int nb = ng * nk;
+    std::vector<int> gl(nb), fl(nb), sl(nb);
+    for (int a = 0; a < ng; ++a) {
+      const int j = (g0 + a) / nsrc, s = (g0 + a) % nsrc;
+      for (int i = 0; i < nk; ++i) {
+        gl[a * nk + i] = (j * nsrc + s) * nk + i;
+        fl[a * nk + i] = j * nk + i;
+        sl[a * nk + i] = s;
+      }
+    }
+    if ((st = set_batch_fs(c, gl, fl, sl)) != HELM_OK) return st;
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, wavelet ? c.wav : nullptr, c.slot_f, c.slot_s,
+                   nb, c.q, c.err + 1, c.st);
+    std::vector<SlotReport> rep, ra;
+    st = solve_batch(c, 0, c.q, c.u, nb, rep);
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
+    result = worst(result, st);
+    // r = sum_i c_i P_r u_i - d per (frequency, source) group, f += 1/2 ||r||^2
+    launch_residual_25d(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.ck, c.slot_f, c.slot_s, nsrc, nk, ng, c.res,
+                        c.f_slot, c.st);
+    launch_sum_f(c.f_slot, c.ident, ng, f_out, 1, c.st);
+    // v_i = -H(k_i)^{-H} P_r^T (c_i r), g += w^2 Re(conj(u_i) v_i)
+    cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+    launch_spread_25d(*P, c.res, rec_idx, nrec, c.ck, c.slot_f, nk, nb, c.q, c.st);
+    st = solve_batch(c, 1, c.q, c.v, nb, ra);
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
+    result = worst(result, st);
+    merge_reports(rep, ra);
+    launch_grad_accum(c.u, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    for (auto& r : rep) result = worst(result, r.status);
+    fill_reports(reports, gl, rep);
+  }
+  launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  return result;
 }
 
 int helm_hessvec(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,

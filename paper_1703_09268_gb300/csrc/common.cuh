@@ -207,7 +207,7 @@ void launch_restrict_model(const double* mf, const LevelGeom& f, double* mc, con
 void launch_extend(const helm_plan& P, const double* m_phys, double* m64, float* m32, cudaStream_t st);
 void launch_tables(const helm_plan& P, int level, const double* freqs_dev, int nfreq,
                    double2* tab64_fwd, double2* tab64_adj, float2* tab32_fwd, float2* tab32_adj,
-                   cudaStream_t st);
+                   cudaStream_t st, const double* shift = nullptr);
 void launch_copy_m32(const double* m64, float* m32, size_t n, cudaStream_t st);
 void launch_sources(const helm_plan& P, const int32_t* src_idx, int n_srcloc, const double2* Q,
                     int nsrc, const double2* wavelet, const int* slot_f, const int* slot_s,
@@ -226,6 +226,12 @@ void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, con
 // b_s = -w_f^2 dmc u_s for slots 0..nslots-1 (linearised state right-hand side)
 void launch_born_source(const double2* u, const double* dmc, const double* w2, const int* slot_f, int nslots,
                         size_t n, double2* b, cudaStream_t st);
+// 2.5D: residual per group of nk slots (one per k_y node) and the weighted adjoint sources
+void launch_residual_25d(const helm_plan& P, const double2* u, const int32_t* rec_idx, int nrec, const double2* d_obs,
+                         const double* ck, const int* slot_f, const int* slot_s, int nsrc, int nk, int ngroups,
+                         double2* res, double* f_grp, cudaStream_t st);
+void launch_spread_25d(const helm_plan& P, const double2* res, const int32_t* rec_idx, int nrec, const double* ck,
+                       const int* slot_f, int nk, int nslots, double2* b, cudaStream_t st);
 void launch_extend_adjoint(const helm_plan& P, const double* gcomp, double* g_phys, cudaStream_t st);
 void launch_sum_f(const double* f_slot, const int* slots, int nslots, double* f_out, int accumulate,
                   cudaStream_t st);

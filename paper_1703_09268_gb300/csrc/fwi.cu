@@ -94,7 +94,7 @@ __device__ double2 inv_eta(const TabArgs& A, int ka, double t0, double omega) {
 __device__ double2 mulc(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ double2 conjc(double2 a) { return make_double2(a.x, -a.y); }
 
-__global__ void k_tables(TabArgs A, const double* __restrict__ omega, int nfreq,
+__global__ void k_tables(TabArgs A, const double* __restrict__ omega, const double* __restrict__ shift, int nfreq,
                          double2* __restrict__ t64f, double2* __restrict__ t64a,
                          float2* __restrict__ t32f, float2* __restrict__ t32a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -114,6 +114,8 @@ __global__ void k_tables(TabArgs A, const double* __restrict__ omega, int nfreq,
     cm = mulc(a_i, b_m); cm.x /= h2; cm.y /= h2;
     cp = mulc(a_i, b_p); cp.x /= h2; cp.y /= h2;
     cd = make_double2(-(cm.x + cp.x), -(cm.y + cp.y));
+    // a constant diagonal shift (2.5D: -k_y^2) rides on the first axis' diagonal
+    if (shift && ka == 0) cd.x -= shift[f];
     // H^H: coefficient of x_{i-1} is conj(cp[i-1]), of x_{i+1} is conj(cm[i+1])
     if (i > 0) {
       const double2 a_l = inv_eta(A, ka, at(i - 1), w);
@@ -254,6 +256,61 @@ __global__ void k_born_source(const double2* __restrict__ u, const double* __res
   b[(size_t)s * n + p] = make_double2(c * uu.x, c * uu.y);
 }
 
+// 2.5D residual of group a (slots a*nk .. a*nk+nk-1, one per k_y node):
+// r = sum_i c_i P_r u_i - d, with c indexed by the slot's virtual frequency;
+// f_grp[a] = 1/2 ||r||^2.
+__global__ void k_residual_25d(GeomArgs g, const double2* __restrict__ u, size_t n,
+                               const int32_t* __restrict__ rec_idx, int nrec, const double2* __restrict__ d_obs,
+                               const double* __restrict__ ck, const int* __restrict__ slot_f,
+                               const int* __restrict__ slot_s, int nsrc, int nk, double2* __restrict__ res,
+                               double* __restrict__ f_grp) {
+  __shared__ double sh[256];
+  const int a = blockIdx.x;
+  const int s0 = a * nk;
+  const int j = slot_f[s0] / nk;
+  const size_t drow = ((size_t)j * nsrc + slot_s[s0]) * nrec;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+    size_t c;
+    double2 v = make_double2(0, 0);
+    if (phys_to_comp(g, rec_idx[k], &c)) {
+      for (int i = 0; i < nk; ++i) {
+        const double w = ck[slot_f[s0 + i]];
+        const double2 ui = u[(size_t)(s0 + i) * n + c];
+        v.x += w * ui.x;
+        v.y += w * ui.y;
+      }
+    }
+    const double2 d = d_obs[drow + k];
+    const double2 r = make_double2(v.x - d.x, v.y - d.y);
+    res[(size_t)a * nrec + k] = r;
+    acc += r.x * r.x + r.y * r.y;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) f_grp[a] = 0.5 * sh[0];
+}
+
+// b_slot += -c_i P_r^T r_group for every slot (its group is slot / nk).
+__global__ void k_spread_25d(GeomArgs g, const double2* __restrict__ res, const int32_t* __restrict__ rec_idx,
+                             int nrec, const double* __restrict__ ck, const int* __restrict__ slot_f, int nk,
+                             int nslots, double2* b, size_t n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (k >= nrec || a >= nslots) return;
+  size_t c;
+  if (!phys_to_comp(g, rec_idx[k], &c)) return;
+  const double w = -ck[slot_f[a]];
+  const double2 r = res[(size_t)(a / nk) * nrec + k];
+  double* dst = (double*)(b + (size_t)a * n + c);
+  atomicAdd(dst, w * r.x);
+  atomicAdd(dst + 1, w * r.y);
+}
+
 // g_phys = E^T gcomp: each physical node sums the computational nodes copying it.
 __global__ void k_extend_adjoint(GeomArgs g, const double* __restrict__ gc, double* __restrict__ gp) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,7 +364,8 @@ void launch_copy_m32(const double* m64, float* m32, size_t n, cudaStream_t st) {
 }
 
 void launch_tables(const helm_plan& P, int level, const double* omega_dev, int nfreq,
-                   double2* t64f, double2* t64a, float2* t32f, float2* t32a, cudaStream_t st) {
+                   double2* t64f, double2* t64a, float2* t32f, float2* t32a, cudaStream_t st,
+                   const double* shift) {
   const LevelGeom& L = P.lev[level];
   TabArgs A;
   const int map3[3] = {0, 1, 2}, map2[3] = {0, 2, -1};
@@ -330,7 +388,7 @@ void launch_tables(const helm_plan& P, int level, const double* omega_dev, int n
   A.h = L.h;
   A.Nmax = L.Nmax;
   dim3 grd((L.Nmax + 127) / 128, 3, nfreq);
-  k_tables<<<grd, 128, 0, st>>>(A, omega_dev, nfreq, t64f, t64a, t32f, t32a);
+  k_tables<<<grd, 128, 0, st>>>(A, omega_dev, shift, nfreq, t64f, t64a, t32f, t32a);
   count_launch();
 }
 
@@ -391,6 +449,23 @@ void launch_born_source(const double2* u, const double* dmc, const double* w2, c
   if (nslots <= 0) return;
   dim3 grd((unsigned)((n + 255) / 256), nslots);
   k_born_source<<<grd, 256, 0, st>>>(u, dmc, w2, slot_f, n, b);
+  count_launch();
+}
+
+void launch_residual_25d(const helm_plan& P, const double2* u, const int32_t* rec_idx, int nrec, const double2* d_obs,
+                         const double* ck, const int* slot_f, const int* slot_s, int nsrc, int nk, int ngroups,
+                         double2* res, double* f_grp, cudaStream_t st) {
+  if (ngroups <= 0) return;
+  k_residual_25d<<<ngroups, 256, 0, st>>>(geom(P), u, P.lev[0].n, rec_idx, nrec, d_obs, ck, slot_f, slot_s, nsrc, nk,
+                                          res, f_grp);
+  count_launch();
+}
+
+void launch_spread_25d(const helm_plan& P, const double2* res, const int32_t* rec_idx, int nrec, const double* ck,
+                       const int* slot_f, int nk, int nslots, double2* b, cudaStream_t st) {
+  if (nslots <= 0) return;
+  dim3 grd((unsigned)((nrec + 127) / 128), nslots);
+  k_spread_25d<<<grd, 128, 0, st>>>(geom(P), res, rec_idx, nrec, ck, slot_f, nk, nslots, b, P.lev[0].n);
   count_launch();
 }
 

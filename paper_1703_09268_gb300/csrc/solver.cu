@@ -135,7 +135,7 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   C.q = bp.take<double2>((size_t)B * n0);
   C.u = bp.take<double2>((size_t)B * n0);
   const bool born = call == HELM_CALL_BORN || call == HELM_CALL_BORN_ADJOINT || call == HELM_CALL_GN_HESSVEC ||
-                    call == HELM_CALL_HESSVEC;
+                    call == HELM_CALL_HESSVEC || call == HELM_CALL_MISFIT_GRAD_25D;
   if (call == HELM_CALL_ADJOINT || call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT || born)
     C.v = bp.take<double2>((size_t)B * n0);
   C.nrm = bp.take<double>(B);
@@ -148,13 +148,19 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   } else {
     layout_hierarchy<double>(bp, P, C.h64, B);
   }
-  if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_MISFIT || call == HELM_CALL_HESSVEC) {
+  if (call == HELM_CALL_MISFIT_GRAD_25D) {
+    C.shift = bp.take<double>(nfreq);
+    C.ck = bp.take<double>(nfreq);
+    C.wav = bp.take<double2>(nfreq);
+  }
+  if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_MISFIT || call == HELM_CALL_HESSVEC ||
+      call == HELM_CALL_MISFIT_GRAD_25D) {
     C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
     C.f_slot = bp.take<double>(B);
   }
   if (call == HELM_CALL_HESSVEC) C.du = bp.take<double2>((size_t)B * n0);
   if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT || call == HELM_CALL_BORN_ADJOINT ||
-      call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC)
+      call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC || call == HELM_CALL_MISFIT_GRAD_25D)
     C.gcomp = bp.take<double>(n0);
   if (call == HELM_CALL_GN_HESSVEC) C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
   if (call == HELM_CALL_BORN || call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC)
@@ -236,7 +242,19 @@ int setup_operator(Ctx& c, const double* m_phys, const double* freqs_hz) {
     launch_copy_m32(c.m64[l], c.m32[l], P.lev[l].n, c.st);
   }
   for (int l = 0; l < L; ++l)
-    launch_tables(P, l, c.omega, c.nfreq, c.tab64[l][0], c.tab64[l][1], c.tab32[l][0], c.tab32[l][1], c.st);
+    launch_tables(P, l, c.omega, c.nfreq, c.tab64[l][0], c.tab64[l][1], c.tab32[l][0], c.tab32[l][1], c.st,
+                  c.shift);
+  return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_E_CUDA;
+}
+
+int set_batch_fs(Ctx& c, const std::vector<int>& g, const std::vector<int>& f, const std::vector<int>& s) {
+  const int nb = (int)g.size();
+  cudaMemcpyAsync(c.slot_f, f.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.st);
+  cudaMemcpyAsync(c.slot_s, s.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.st);
+  cudaMemcpyAsync(c.slot_g, g.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.st);
+  std::vector<int> a(nb);
+  for (int i = 0; i < nb; ++i) a[i] = i;
+  set_active(c, a);
   return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_E_CUDA;
 }
 

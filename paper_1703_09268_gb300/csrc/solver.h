@@ -77,6 +77,9 @@ struct Ctx {
   double* gcomp = nullptr;
   double* dmc = nullptr;   // extended model perturbation E dm (linearised calls)
   double2* du = nullptr;   // linearised state / adjoint (full Hessian product)
+  double* shift = nullptr; // [nfreq] diagonal shift per (virtual) frequency (2.5D: k_y^2), or null
+  double* ck = nullptr;    // [nfreq] 2.5D quadrature weight per virtual frequency
+  double2* wav = nullptr;  // [nfreq] 2.5D wavelet per virtual frequency
   // Krylov hierarchies
   Hierarchy<float> h32;
   Hierarchy<double> h64;
@@ -100,6 +103,8 @@ struct SlotReport {
 int setup_operator(Ctx& c, const double* m_phys, const double* freqs_hz);
 // Set the current batch: slots 0..nb-1 take global (k, s) indices g[0..nb-1].
 int set_batch(Ctx& c, const std::vector<int>& g);
+// The same with explicit (frequency, source) per slot; g are the report indices.
+int set_batch_fs(Ctx& c, const std::vector<int>& g, const std::vector<int>& f, const std::vector<int>& s);
 void set_active(Ctx& c, const std::vector<int>& a);
 // Solve H u = q (dir 0) or H^H u = q (dir 1) for all slots of the batch;
 // q and u are FP64 batch arrays.  Fills rep[0..nb-1].

@@ -265,7 +265,7 @@ def test_pin_catches_wrong_sign_of_ky_shift(monkeypatch):
 
 
 def test_pin_catches_unweighted_adjoint_source(monkeypatch):
-    """v_i = -H_i^{-H} P^T r without the quadrature weight c_i."""
+    """The gradient evaluated without the quadrature weights c_i."""
     real = O.misfit_and_gradient_25d
 
     def unweighted(g, m_phys, freqs_hz, ky, ck, *a, **k):
