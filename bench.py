@@ -59,7 +59,8 @@ def parse():
     p.add_argument("--workers", type=int, default=4, help="batch mode: models in flight together")
     p.add_argument("--op", default="misfit_grad", choices=["misfit_grad", "gn", "hess"],
                    help="step mode: misfit + gradient, the Gauss-Newton product J^T J dm, or the full Hessian product")
-    p.add_argument("--mode", default="step", choices=["step", "apply", "batch"],
+    p.add_argument("--nk", type=int, default=16, help="2.5D mode: k_y quadrature nodes")
+    p.add_argument("--mode", default="step", choices=["step", "apply", "batch", "25d"],
                    help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
                         "workload's 16 complex64 fields)")
     return p.parse_args()
@@ -299,6 +300,76 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(sm))
 
 
+def run_25d(args):
+    """2.5D misfit + gradient on a 401 x 201 layered x-z model: each (source,
+    frequency) pair is nk shifted 2D solves and nk adjoint solves."""
+    import torch
+    from paper_1703_09268_gb300 import helm, synth
+
+    dev = torch.device("cuda", 0)
+    wl = synth.workload_25d()
+    grid = helm.make_grid(2, wl.n, wl.h, wl.npml, wl.v_ref, levels=2)
+    kso, ksi, kco, kci = (int(v) for v in args.smoother.split(","))
+    mk = lambda prec, tol: helm.Plan(grid, helm.default_opts(  # noqa: E731
+        precision=prec, precond=helm.PRECOND_MLGMRES, k_inner=args.k_inner or 10, tol=tol, max_cycles=400,
+        tol_inner=args.tol_inner, k_so=kso, k_si=ksi, k_co=kco, k_ci=kci, max_batch=args.max_batch), device=dev)
+    plan = mk(helm.MIXED if args.precision == "mixed" else helm.FP64, args.tol)
+    # Gauss-Legendre k_y nodes on [0, 1.2 w / v_min] (Sec. 3, 2.5D), receivers in the sources' plane
+    om = 2 * np.pi * wl.freqs_hz[0]
+    t, w = np.polynomial.legendre.leggauss(args.nk)
+    kmax = 1.2 * om / wl.meta["vmin"]
+    ky = 0.5 * kmax * (t + 1)
+    ck = 0.5 * kmax * w / np.pi
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    m0 = T(wl.m0.ravel(), torch.float64)
+    src, Q, rec = T(wl.src_idx, torch.int32), T(wl.Q, torch.complex128), T(wl.rec_idx, torch.int32)
+    rng = np.random.default_rng(9)
+    d_obs = T(1e-4 * (rng.standard_normal((1, wl.nsrc, wl.nrec)) + 1j * rng.standard_normal((1, wl.nsrc, wl.nrec))),
+              torch.complex128)
+    step = lambda p: helm.misfit_and_gradient_25d(p, m0, wl.freqs_hz, ky, ck, src, Q, rec, d_obs)  # noqa: E731
+    for _ in range(args.warmup):
+        step(plan)
+    torch.cuda.synchronize()
+    launches0 = helm.kernel_launch_count()
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, g, rep = step(plan)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = helm.kernel_launch_count() - launches0
+    ms = float(np.mean(times))
+    units = wl.nsrc * wl.nfreq
+    helm.profile_enable(True)
+    step(plan)
+    torch.cuda.synchronize()
+    prof = helm.profile_read()
+    helm.profile_enable(False)
+    hbm, hbm_kind = peaks()
+    tot = sum(v["ms"] for v in prof.values())
+    dom = max((k for k in prof if prof[k]["bytes"] > 0), key=lambda k: prof[k]["ms"])
+    achieved = prof[dom]["bytes"] / (prof[dom]["ms"] / 1e3) / 1e9
+    f64, g64, _ = step(mk(helm.FP64, 1e-13))
+    out = dict(mode="25d", metric="2.5D misfit+gradient (src\u00b7freq)/s", value=round(units / (ms / 1e3), 3),
+               unit=UNIT, ms_per_step=round(ms, 3), steps=args.steps, warmup=args.warmup, n_gpus=1,
+               config=dict(workload=wl.name, grid_comp=list(plan.N), nk=args.nk, kmax=round(kmax, 6),
+                           sources=wl.nsrc, receivers=wl.nrec, solves_per_step=2 * args.nk * units,
+                           data="seeded random observed data (the work does not depend on it)"),
+               roofline=dict(bound="hbm", kernel=dom, achieved=round(achieved, 1), peak=hbm, peak_kind=hbm_kind,
+                             unit="GB/s", frac=round(achieved / hbm, 3),
+                             share={k: round(v["ms"] / tot, 3) for k, v in prof.items() if v["launches"]}),
+               gpu_launches=int(launches),
+               solver=dict(outer_iters_per_solve_pair=float(np.mean([r["iters"] for r in rep]))),
+               accuracy=dict(reference="FP64 GPU path to rel. residual 1e-13",
+                             f_rel_err=float(abs(f.item() - f64.item()) / abs(f64.item())),
+                             g_rel_err=float((g - g64).norm().item() / g64.norm().item())))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -307,6 +378,8 @@ def main():
         return run_apply(args)
     if args.mode == "batch":
         return run_batch(args)
+    if args.mode == "25d":
+        return run_25d(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

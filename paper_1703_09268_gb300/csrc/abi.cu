@@ -139,7 +139,8 @@ static int build_plan(const helm_grid* g, const helm_solve_opts* o, helm_plan* P
     if (g->dim == 3) {
       L.K[0] = L.N[0]; L.K[1] = L.N[1]; L.K[2] = L.N[2];
     } else {
-      L.K[0] = L.N[0]; L.K[1] = L.N[2]; L.K[2] = 1;
+      // 2D: x, a unit axis, z -- the stencil's flattened plane is one x row and it marches in z
+      L.K[0] = L.N[0]; L.K[1] = 1; L.K[2] = L.N[2];
     }
     L.n = (size_t)L.N[0] * L.N[1] * L.N[2];
     L.Nmax = std::max(L.K[0], std::max(L.K[1], L.K[2]));

@@ -87,7 +87,7 @@ struct ProfScope {
 // ---------------------------------------------------------------------------
 struct LevelGeom {
   int N[3];        // computational nodes per physical axis (x, y, z)
-  int K[3];        // the same sizes in kernel order (2D: x, z, 1)
+  int K[3];        // the same sizes in kernel order (2D: x, 1, z)
   size_t n;        // nodes of one field
   int Nmax;        // table row length
   double h;        // spacing at this level

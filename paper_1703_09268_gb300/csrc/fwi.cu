@@ -58,7 +58,7 @@ __global__ void k_copy_m32(const double* __restrict__ a, float* __restrict__ b, 
 }
 
 // Damping-layer tables of one level.  Kernel axis ka maps to physical axis
-// pax[ka] (or -1 for the unused third axis of 2D problems).
+// pax[ka] (or -1 for the unit middle axis of 2D problems).
 struct TabArgs {
   int pax[3];
   int N[3];          // level sizes per kernel axis
@@ -368,7 +368,7 @@ void launch_tables(const helm_plan& P, int level, const double* omega_dev, int n
                    const double* shift) {
   const LevelGeom& L = P.lev[level];
   TabArgs A;
-  const int map3[3] = {0, 1, 2}, map2[3] = {0, 2, -1};
+  const int map3[3] = {0, 1, 2}, map2[3] = {0, -1, 2};
   for (int ka = 0; ka < 3; ++ka) {
     const int pa = P.g.dim == 3 ? map3[ka] : map2[ka];
     A.pax[ka] = pa;

@@ -2,7 +2,7 @@
 // linear interpolation P (coarse node j sits on fine node 2j+1; even fine
 // nodes average their two coarse neighbours, zero beyond the walls) and the
 // full-weighting restriction R = 2^-dim P^T (1D weights 1/4, 1/2, 1/4).
-// A kernel axis of size 1 (the third axis of 2D problems) is not coarsened.
+// A kernel axis of size 1 (the middle axis of 2D problems) is not coarsened.
 #include "common.cuh"
 
 namespace helm {

@@ -152,6 +152,28 @@ def workload_2d(seed: int = 1, n: int = 101, h: float = 10.0, npml: int = 20) ->
         meta={"seed": seed})
 
 
+def workload_25d(seed: int = 6, nx: int = 401, nz: int = 201, h: float = 10.0, npml: int = 20,
+                 nsrc: int = 32, freq: float = 8.0) -> Workload:
+    """2.5D (a y-invariant model on the x-z plane): 401 x 201, h = 10 m, 20-cell
+    layers, 8 seeded layers (1500-4500 m/s, smoothed sigma = 2 cells) plus one
+    Gaussian inclusion as the true model, evaluated at the sigma = 6 smoothed
+    model; nsrc sources spread along z = 2 cells, receivers at every x of that
+    row (in the sources' plane), one frequency."""
+    rng = np.random.default_rng(seed)
+    dims = (nx, 1, nz)
+    v = layered_velocity(rng, dims, nlayers=8, smooth=2.0)
+    zz, xx = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    vt = v + 300.0 * np.exp(-((xx - nx / 2.0) ** 2 + (zz - nz / 2.0) ** 2) / (2 * (nz / 8.0) ** 2))[:, None, :]
+    v0 = _gaussian_smooth(v[:, 0, :], 6.0)[:, None, :]
+    xs = np.linspace(nx / (2 * nsrc), nx - nx / (2 * nsrc), nsrc).round().astype(int)
+    src_idx, Q = point_sources(dims, [(int(x), 0, 2) for x in xs])
+    rec_idx = surface_receivers(dims, 2)
+    return Workload(
+        name=f"2.5d-{nx}x{nz}-h{h:g}-pml{npml}-{freq:g}Hz-{nsrc}src", dim=2, n=dims, h=h, npml=(npml, 0, npml),
+        v_ref=3000.0, freqs_hz=np.array([freq]), m_true=slowness2(vt), m0=slowness2(v0), src_idx=src_idx, Q=Q,
+        rec_idx=rec_idx, meta={"seed": seed, "vmin": float(v0.min())})
+
+
 def workload_3d_layered(seed: int = 2, n: int = 64, h: float = 25.0, npml: int = 10,
                         nsrc_side: int = 4, freq: float = 4.0) -> Workload:
     """3D n^3 layered model (8 seeded layers, 1500-4500 m/s, smoothed sigma=2 cells)
