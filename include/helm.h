@@ -393,7 +393,7 @@ typedef enum {
   HELM_PROF_STENCIL_C128 = 1, /* stencil / residual, complex128 */
   HELM_PROF_KRYLOV_C64 = 2,   /* fused Gram-Schmidt / norm / update passes, complex64 */
   HELM_PROF_KRYLOV_C128 = 3,  /* the same in complex128 */
-  HELM_PROF_SMALL = 4,        /* per-right-hand-side reductions and Hessenberg updates */
+  HELM_PROF_SMALL = 4,        /* unused (reductions are folded into the producing kernels); kept for stable numbering */
   HELM_PROF_TRANSFER = 5,     /* restriction / prolongation */
   HELM_PROF_FWI = 6,          /* sources, receivers, misfit, gradient, extension */
   HELM_PROF_MISC = 7,         /* conversions, zero fills, Jacobi */

@@ -440,6 +440,7 @@ void launch_spread(const helm_plan& P, const double2* r, size_t r_stride, const 
 void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
                        const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st) {
   if (nslots <= 0) return;
+  ProfScope ps(PC_FWI, (double)nslots * n * 2 * sizeof(double2) + (double)n * 2 * sizeof(double), st);
   k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n, gcomp);
   count_launch();
 }
@@ -447,6 +448,7 @@ void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, con
 void launch_born_source(const double2* u, const double* dmc, const double* w2, const int* slot_f, int nslots,
                         size_t n, double2* b, cudaStream_t st) {
   if (nslots <= 0) return;
+  ProfScope ps(PC_FWI, (double)nslots * n * 2 * sizeof(double2) + (double)n * sizeof(double), st);
   dim3 grd((unsigned)((n + 255) / 256), nslots);
   k_born_source<<<grd, 256, 0, st>>>(u, dmc, w2, slot_f, n, b);
   count_launch();
