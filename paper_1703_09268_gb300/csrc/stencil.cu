@@ -19,6 +19,7 @@
 // products with Krylov basis vectors (the first Gram-Schmidt pass of an
 // Arnoldi step) or the norm of a residual (reduce.cuh).
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace helm {
 
@@ -36,8 +37,11 @@ struct TileGeom {
 
 // Plain apply (no reduction): one tile per block, grid (tiles, active slots).
 // The tile's z coefficients sit in shared memory and, in single precision,
-// the z march is fully unrolled (no register rotation between planes).
-template <typename R, bool RESID>
+// the z march is fully unrolled (no register rotation between planes).  With
+// PF > 0 (x 16-byte aligned) thread 0 bulk-prefetches into L2, one plane at a
+// time, the tile's window of x PF planes ahead of the march: the bytes in
+// flight no longer depend on registers.
+template <typename R, bool RESID, int PF>
 __global__ void __launch_bounds__(STPB, 6)
 k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
                 const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
@@ -101,6 +105,18 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
       s2n = hs ? xn[-K0] : zero;
       n2n = hn ? xn[K0] : zero;
       m2 = mq[P];
+    }
+    if (PF > 0 && threadIdx.x == 0 && z + PF < G.K2) {
+      // plane z+PF, columns [seg*STPB - K0, seg*STPB + STPB + K0) clipped to the plane, rounded out
+      // to 16-byte bounds without leaving this slot's field (the element before an odd-aligned
+      // field start belongs to the previous slot, or the start is even)
+      const size_t fb = (size_t)s * G.n, pz = fb + (size_t)(z + PF) * P;
+      const size_t lo = pz + (size_t)max(0, seg * STPB - K0);
+      const size_t hi = pz + (size_t)min(P, seg * STPB + STPB + K0);
+      const size_t a0 = lo & ~(size_t)1;
+      size_t a1 = (hi + 1) & ~(size_t)1;
+      if (a1 > fb + G.n) a1 -= 2;
+      if (a1 > a0) bulk_prefetch_l2(x + a0, (uint32_t)((a1 - a0) * sizeof(C)));
     }
     const C zm = stz[0][zz], zd = stz[1][zz], zp = stz[2][zz];
     const C diag = mkc(dre + zd.x + om2 * mm, dim + zd.y);
@@ -349,12 +365,21 @@ void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int 
   }
   dim3 grd(nblk, na);
   if (e.kind == EPI_NONE) {
-    if (b)
-      k_stencil_plain<R, true><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m, op.w2,
-                                                     slot_f, act, G);
+    // L2 prefetch 4 planes ahead: single precision (the FP64 stencil is ALU-bound), 16-byte aligned x,
+    // grids that do not sit in L2 anyway
+    const bool pf = sizeof(R) == 4 && ((uintptr_t)x & 15) == 0 && op.n >= PROF_COARSE_N;
+    if (b && pf)
+      k_stencil_plain<R, true, 4><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
+                                                        op.w2, slot_f, act, G);
+    else if (b)
+      k_stencil_plain<R, true, 0><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
+                                                        op.w2, slot_f, act, G);
+    else if (pf)
+      k_stencil_plain<R, false, 4><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
+                                                         op.w2, slot_f, act, G);
     else
-      k_stencil_plain<R, false><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m, op.w2,
-                                                      slot_f, act, G);
+      k_stencil_plain<R, false, 0><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
+                                                         op.w2, slot_f, act, G);
   } else if (b) {
     stencil_red<R, true>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
   } else {
