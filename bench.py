@@ -185,10 +185,10 @@ def _oracle_worker(args):
 
 
 # DRAM traffic of the single-precision stencil from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of k_stencil_plain<float, 0, 4>,
-# 16 fields of 85^3; profiles/stencil_c64_85cubed_16fields.md).  It scales with
-# the points a launch processes.  None when no capture matches the current
-# kernel.
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_stencil_plain<float, 0, 4>
+# on 16 fields of 85^3, `bench.py --mode apply`).  It scales with the points a
+# launch processes.  Set to None when the kernel changes until it is captured
+# again.
 STENCIL_TRAFFIC = dict(kernel="k_stencil_plain<float, 0, 4>", dram_bytes=81.184768e6 + 40.391424e6,
                        algorithmic_bytes=16 * 614125 * 16 + 614125 * 4)
 

@@ -23,7 +23,7 @@ Environment for Nonlinear Inverse Problems"):
     FGMRES, rediscretised coarse operators) and damped Jacobi as
     preconditioners.
 
-Readings taken where the paper is silent (each also listed in the design doc):
+Readings taken where the paper is silent:
   * m = 1/v^2 and H = L_eta + w^2 diag(m);
   * eta_d(x) = 1 + i sigma_d(x)/w with sigma = sigma_max (dist/W)^2, W the
     layer width on that side, sigma_max = 3 v_ref ln(1000) / (2 npml h);
