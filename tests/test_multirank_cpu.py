@@ -96,3 +96,39 @@ def test_late_rank_is_dropped_after_deadline(tmp_path):
     assert got[0] == pytest.approx(f0, rel=1e-13)
     assert np.allclose(got[1:1 + n], g0.ravel())
     assert list(got[1 + n:]) == [0.0]
+
+
+def _worker_gn(rank, world, port, out):
+    """Each rank applies the Gauss-Newton and full Hessian products on its
+    share of the (frequency, source) pairs; one all-reduce sums them."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    g, m0, freqs, src, Q, rec, d = _problem()
+    nf, ns = len(freqs), Q.shape[1]
+    mask = np.zeros((nf, ns), dtype=bool)
+    for p in parallel.shard(nf * ns, rank, world):
+        mask[p // ns, p % ns] = True
+    dm = np.random.default_rng(5).standard_normal(g.n_phys) * 1e-8
+    gn = O.gauss_newton_hessvec(g, m0, freqs, src, Q, rec, dm, mask=mask).ravel()
+    hv = O.hessvec(g, m0, freqs, src, Q, rec, d, dm, mask=mask).ravel()
+    t = [torch.from_numpy(gn.copy()), torch.from_numpy(hv.copy())]
+    parallel.allreduce_sum(t)
+    if rank == 0:
+        np.save(out, np.concatenate([t[0].numpy(), t[1].numpy()]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_hessian_products_equal_single_rank(tmp_path):
+    """The linearised calls shard like the gradient: per-pair sums plus one
+    all-reduce (Gauss-Newton and full Hessian products)."""
+    out = str(tmp_path / "gn.npy")
+    mp.spawn(_worker_gn, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    g, m0, freqs, src, Q, rec, d = _problem()
+    dm = np.random.default_rng(5).standard_normal(g.n_phys) * 1e-8
+    gn = O.gauss_newton_hessvec(g, m0, freqs, src, Q, rec, dm).ravel()
+    hv = O.hessvec(g, m0, freqs, src, Q, rec, d, dm).ravel()
+    n = gn.size
+    assert np.allclose(got[:n], gn, rtol=1e-12, atol=1e-12 * np.abs(gn).max())
+    assert np.allclose(got[n:], hv, rtol=1e-12, atol=1e-12 * np.abs(hv).max())
