@@ -108,3 +108,56 @@ def test_status_strings(helm):
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert L.helm_status_string(code)
     assert L.helm_status_string(123) == b"unknown status"
+
+
+def test_workspace_sizes_of_the_other_calls(helm):
+    p = helm.Plan(helm.make_grid(3, (16, 16, 16), 25.0, (4, 4, 4), 3000.0, levels=2), helm.default_opts(),
+                  device="cpu")
+    m = p.workspace_size(helm.CALL_MISFIT_GRAD, 1, 8, 16)
+    pre = p.workspace_size(helm.CALL_PRECOND, 1, 8, 0)
+    born = p.workspace_size(helm.CALL_BORN, 1, 8, 16)
+    gn = p.workspace_size(helm.CALL_GN_HESSVEC, 1, 8, 16)
+    hv = p.workspace_size(helm.CALL_HESSVEC, 1, 8, 16)
+    # the preconditioner alone needs neither the outer basis nor the FP64 fields
+    assert 0 < pre < m
+    # the Gauss-Newton product keeps the linearised data, the full Hessian one more field
+    assert pre < born < gn < hv
+    p2 = helm.Plan(helm.make_grid(2, (31, 1, 21), 10.0, (5, 0, 5), 2000.0, levels=2), helm.default_opts(),
+                   device="cpu")
+    w1 = p2.workspace_size(helm.CALL_MISFIT_GRAD_25D, 4, 3, 11)
+    w2 = p2.workspace_size(helm.CALL_MISFIT_GRAD_25D, 8, 3, 11)
+    assert 0 < w1 < w2
+    with pytest.raises(helm.HelmError):
+        p.workspace_size(helm.CALL_MISFIT_GRAD_25D + 1, 1, 1, 1)
+
+
+def test_new_calls_reject_bad_arguments_before_any_device_work(helm):
+    """Null pointers, empty sizes, a 3D plan for 2.5D and non-finite wavenumbers
+    are refused with HELM_E_INVAL on the host (no CUDA call is made)."""
+    L = helm.lib()
+    p3 = helm.Plan(helm.make_grid(3, (8, 8, 8), 25.0, (2, 2, 2), 3000.0), helm.default_opts(precond=0),
+                   device="cpu")
+    fr = (ctypes.c_double * 1)(5.0)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks fail before any use
+    rep = (helm.HelmRhsReport * 4)()
+    # helm_born without dm
+    assert L.helm_born(p3._h, fake, fr, 1, fake, 1, fake, 1, None, fake, 1, None, None, fake, fake, 1 << 20,
+                       rep, None) == helm.HELM_E_INVAL
+    # helm_born_adjoint without dD
+    assert L.helm_born_adjoint(p3._h, fake, fr, 1, fake, 1, fake, 1, None, fake, 1, None, None, fake, fake, 1 << 20,
+                               rep, None) == helm.HELM_E_INVAL
+    # helm_hessvec without d_obs
+    assert L.helm_hessvec(p3._h, fake, fr, 1, fake, 1, fake, 1, None, fake, 1, None, fake, None, fake, fake,
+                          1 << 20, rep, None) == helm.HELM_E_INVAL
+    # helm_precond_apply with no fields
+    assert L.helm_precond_apply(p3._h, fake, 5.0, 0, fake, fake, 0, fake, 1 << 20, None) == helm.HELM_E_INVAL
+    # 2.5D needs a 2D plan, nk >= 1 and finite wavenumbers
+    ky = (ctypes.c_double * 2)(0.01, 0.02)
+    ck = (ctypes.c_double * 2)(0.5, 0.5)
+    args = (fake, 1, fake, 1, None, fake, 1, fake, fake, fake, fake, 1 << 20, rep, None)
+    assert L.helm_misfit_and_gradient_25d(p3._h, fake, fr, 1, ky, ck, 2, *args) == helm.HELM_E_INVAL
+    p2 = helm.Plan(helm.make_grid(2, (11, 1, 9), 25.0, (3, 0, 3), 3000.0), helm.default_opts(precond=0),
+                   device="cpu")
+    assert L.helm_misfit_and_gradient_25d(p2._h, fake, fr, 1, ky, ck, 0, *args) == helm.HELM_E_INVAL
+    bad = (ctypes.c_double * 2)(0.01, float("nan"))
+    assert L.helm_misfit_and_gradient_25d(p2._h, fake, fr, 1, bad, ck, 2, *args) == helm.HELM_E_INVAL
