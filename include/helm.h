@@ -19,7 +19,10 @@
  * Solves are matrix-free: restarted FGMRES (Sec. 4) with the multi-level
  * ML-GMRES preconditioner of Sec. 4 (Alg. vcycle; Fig. mlgmres) or damped
  * Jacobi, in FP64 or with complex64 inner solves under FP64 iterative
- * refinement.
+ * refinement.  Around the objective the library offers the operator and
+ * preconditioner applies, forward and adjoint modelling, the linearised
+ * products of Table derivstuff (J dm, J^T dD, the Gauss-Newton and the full
+ * Hessian-vector products) and 2.5D modelling (Sec. 3).
  *
  * Conventions for every call
  *  - Bulk arrays are DEVICE pointers owned by the caller; the library never
