@@ -557,6 +557,67 @@ def hessvec(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, dm_phys, wave
 
 
 # ---------------------------------------------------------------------------
+# Waveform Reconstruction Inversion (Sec. 3, penalty method; Appendix B):
+# the field minimises ||P_r u - d||^2 + lambda^2 ||H u - q||^2 for fixed m
+# ---------------------------------------------------------------------------
+
+def wri_field(H: sp.spmatrix, P: sp.spmatrix, q: np.ndarray, d: np.ndarray, lam: float) -> np.ndarray:
+    """u(m) of eq. (wrifieldeq) from its normal equations
+    (P_r^T P_r + lambda^2 H^H H) u = P_r^T d + lambda^2 H^H q (sparse LU)."""
+    H = sp.csc_matrix(H)
+    Gm = sp.csc_matrix(P.T @ P + lam * lam * (H.conj().T @ H))
+    rhs = P.T @ d + lam * lam * (H.conj().T @ q)
+    return spla.spsolve(Gm, rhs)
+
+
+def wri_field_dataspace(H: sp.spmatrix, P: sp.spmatrix, q: np.ndarray, d: np.ndarray, lam: float) -> np.ndarray:
+    """The same field through solves with H and H^H only:
+    u = u0 + lambda^-2 H^{-1} H^{-H} P^T z with u0 = H^{-1} q and
+    (I + lambda^-2 P H^{-1} H^{-H} P^T) z = d - P u0 (the push-through identity
+    applied to the normal equations; a dense nrec x nrec system here)."""
+    S = DirectSolver(H)
+    u0 = S.solve(q)
+    nrec = P.shape[0]
+    C = np.zeros((nrec, nrec), dtype=np.complex128)
+    for k in range(nrec):
+        e = np.zeros(nrec, dtype=np.complex128)
+        e[k] = 1.0
+        C[:, k] = P @ S.solve(S.solve_adjoint(P.T @ e))
+    z = np.linalg.solve(np.eye(nrec) + C / (lam * lam), d - P @ u0)
+    return u0 + S.solve(S.solve_adjoint(P.T @ z)) / (lam * lam)
+
+
+def wri_misfit_and_gradient(g: Grid, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, lam: float):
+    """WRI objective f = sum 1/2 ||P_r u - d||^2 + lambda^2/2 ||H u - q||^2 at
+    u = u(m) and its gradient lambda^2 E^T sum Re(T^* (H u - q)) =
+    E^T sum lambda^2 w^2 Re(conj(u) (H u - q)) (Appendix B, variable projection)."""
+    mc = extend(g, m_phys)
+    Qa = np.asarray(Q)
+    d_obs = np.asarray(d_obs, dtype=np.complex128)
+    P = receiver_matrix(g, rec_idx)
+    f = 0.0
+    gc = np.zeros(g.size)
+    for k, fr in enumerate(freqs_hz):
+        om = _omega(fr)
+        H = helmholtz_matrix(g, mc, om)
+        q = source_fields(g, src_idx, Qa)
+        for s in range(Qa.shape[1]):
+            u = wri_field(H, P, q[s], d_obs[k, s], lam)
+            ru = H @ u - q[s]
+            rd = P @ u - d_obs[k, s]
+            f += 0.5 * float(np.vdot(rd, rd).real) + 0.5 * lam * lam * float(np.vdot(ru, ru).real)
+            gc += lam * lam * om * om * np.real(np.conj(u) * ru)
+    return f, extend_adjoint(g, gc)
+
+
+def receiver_matrix(g: Grid, rec_idx) -> sp.csr_matrix:
+    """P_r as a sparse nrec x size matrix (point sampling)."""
+    cols = comp_index(g, np.asarray(rec_idx))
+    n = len(cols)
+    return sp.csr_matrix((np.ones(n), (np.arange(n), cols)), shape=(n, g.size), dtype=np.complex128)
+
+
+# ---------------------------------------------------------------------------
 # 2.5D modelling (Sec. 3, "2.5D"): a y-invariant model, a Fourier transform in
 # y, one 2D problem per wavenumber k_y with the shift -k_y^2, and a quadrature
 # sum over k_y

@@ -276,3 +276,23 @@ def test_pin_catches_unweighted_adjoint_source(monkeypatch):
     monkeypatch.setattr(O, "misfit_and_gradient_25d", unweighted)
     with pytest.raises(AssertionError):
         T25.test_25d_gradient_matches_central_differences()
+
+
+# ---------------------------------------------------------------------------
+# WRI pins (tests/test_oracle_wri.py)
+# ---------------------------------------------------------------------------
+
+import tests.test_oracle_wri as TW  # noqa: E402
+
+
+def test_pin_catches_wri_gradient_without_penalty_weight(monkeypatch):
+    """grad f = T^*(H u - q) without the lambda^2 factor."""
+    real = O.wri_misfit_and_gradient
+
+    def no_lam2(g, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, lam):
+        f, gr = real(g, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, lam)
+        return f, gr / (lam * lam)
+
+    monkeypatch.setattr(O, "wri_misfit_and_gradient", no_lam2)
+    with pytest.raises(AssertionError):
+        TW.test_wri_gradient_matches_central_differences(inspect.unwrap(TW.wri)())
