@@ -70,7 +70,8 @@ typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGM
 typedef enum {
   HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
   HELM_CALL_MISFIT = 4, HELM_CALL_GRADIENT = 5, HELM_CALL_PRECOND = 6, HELM_CALL_BORN = 7,
-  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9, HELM_CALL_HESSVEC = 10, HELM_CALL_MISFIT_GRAD_25D = 11
+  HELM_CALL_BORN_ADJOINT = 8, HELM_CALL_GN_HESSVEC = 9, HELM_CALL_HESSVEC = 10, HELM_CALL_MISFIT_GRAD_25D = 11,
+  HELM_CALL_WRI = 12
 } helm_call;
 
 /* Geometry of the extended domain (Sec. 2: Omega' contains Omega; "PDEopts"
@@ -284,6 +285,25 @@ int helm_misfit_and_gradient_25d(helm_plan* plan, const double* m_phys, const do
                                  int n_srcloc, const void* Q, int nsrc, const void* wavelet,
                                  const int32_t* rec_idx, int nrec, const void* d_obs, double* f_out,
                                  double* g_out, void* workspace, size_t ws_bytes, helm_rhs_report* reports,
+                                 helm_stream_t stream);
+
+/* Waveform Reconstruction Inversion objective and gradient (Sec. 3 penalty
+ * method, eqs. (wri), (wrifieldeq); Appendix B).  For every (k, s) pair the
+ * field u minimises ||P_r u - d||^2 + lambda^2 ||H u - q||^2; with
+ * u0 = H^{-1} q it is u = u0 + lambda^-2 H^{-1} H^{-H} P_r^T z, where z solves
+ * the receiver-space system (I + lambda^-2 P_r H^{-1} H^{-H} P_r^T) z = d - P_r u0
+ * by conjugate gradients (Hermitian positive definite; two solves per
+ * iteration, to a relative residual cg_tol or cg_maxit iterations).  Then
+ *   f = sum 1/2 ||P_r u - d||^2 + lambda^2/2 ||H u - q||^2,
+ *   g = E^T sum lambda^2 w^2 Re(conj(u) (H u - q))   (variable projection).
+ * Arguments as misfit_and_gradient (no mask) plus lambda > 0, cg_tol > 0 and
+ * cg_maxit >= 1.  Pairs whose CG misses cg_tol report HELM_E_NOCONV.
+ * Workspace: helm_workspace_size with HELM_CALL_WRI. */
+int helm_wri_misfit_and_gradient(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
+                                 const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc,
+                                 const void* wavelet, const int32_t* rec_idx, int nrec, const void* d_obs,
+                                 double lambda, double cg_tol, int cg_maxit, double* f_out, double* g_out,
+                                 void* workspace, size_t ws_bytes, helm_rhs_report* reports,
                                  helm_stream_t stream);
 
 /* Misfit alone (Table derivcosts: one PDE per source and frequency):

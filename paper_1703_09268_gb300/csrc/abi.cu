@@ -245,7 +245,7 @@ int helm_plan_dims(const helm_plan* P, int N[3], size_t* n_comp, size_t* n_phys)
 
 int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int nrec, size_t* bytes) {
   if (!P || !bytes || nfreq < 1 || nsrc < 1 || nrec < 0) return HELM_E_INVAL;
-  if (call < HELM_CALL_APPLY || call > HELM_CALL_MISFIT_GRAD_25D) return HELM_E_INVAL;
+  if (call < HELM_CALL_APPLY || call > HELM_CALL_WRI) return HELM_E_INVAL;
   *bytes = layout(*P, call, nfreq, nsrc, nrec, nullptr, nullptr);
   return HELM_OK;
 }
@@ -665,6 +665,101 @@ int helm_misfit_and_gradient_25d(helm_plan* P, const double* m_phys, const doubl
     launch_grad_accum(c.u, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
     for (auto& r : rep) result = worst(result, r.status);
     fill_reports(reports, gl, rep);
+  }
+  launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
+  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  return result;
+}
+
+int helm_wri_misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
+                                 const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
+                                 const int32_t* rec_idx, int nrec, const void* d_obs, double lambda, double cg_tol,
+                                 int cg_maxit, double* f_out, double* g_out, void* ws, size_t ws_bytes,
+                                 helm_rhs_report* reports, helm_stream_t stream) {
+  int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
+  if (st != HELM_OK) return st;
+  if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out || !g_out) return HELM_E_INVAL;
+  if (!(lambda > 0.0) || !std::isfinite(lambda) || !(cg_tol > 0.0) || !std::isfinite(cg_tol) || cg_maxit < 1)
+    return HELM_E_INVAL;
+  Ctx c;
+  if ((st = bind(P, HELM_CALL_WRI, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
+  if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
+  if ((st = check_indices(c, src_idx, n_srcloc, rec_idx, nrec)) != HELM_OK) return st;
+  const int nrhs = nfreq * nsrc;
+  const size_t n = P->lev[0].n;
+  const double inv_l2 = 1.0 / (lambda * lambda);
+  if (reports)
+    for (int i = 0; i < nrhs; ++i) reports[i] = helm_rhs_report{HELM_OK, 0, 0, 0.0};
+  cudaMemsetAsync(c.gcomp, 0, sizeof(double) * n, c.st);
+  cudaMemsetAsync(f_out, 0, sizeof(double), c.st);
+  int result = HELM_OK;
+  for (int start = 0; start < nrhs; start += c.B) {
+    const int nb = std::min(c.B, nrhs - start);
+    std::vector<int> g(nb);
+    for (int a = 0; a < nb; ++a) g[a] = start + a;
+    if ((st = set_batch(c, g)) != HELM_OK) return st;
+    std::vector<SlotReport> rep, r2;
+    auto solve = [&](int dir, const double2* rhs, double2* out) {
+      st = solve_batch(c, dir, rhs, out, nb, r2);
+      if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return false;
+      result = worst(result, st);
+      merge_reports(rep, r2);
+      return true;
+    };
+    auto sources = [&]() {
+      cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+      launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, (const double2*)wavelet, c.slot_f, c.slot_s,
+                     nb, c.q, c.err + 1, c.st);
+    };
+    // u0 = H^{-1} q; receiver residual r0 = d - P_r u0
+    sources();
+    st = solve_batch(c, 0, c.q, c.u, nb, rep);
+    if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
+    result = worst(result, st);
+    launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.slot_f, c.slot_s, nsrc, c.ident, nb,
+                           c.res, c.f_slot, c.st);
+    launch_wri_init(c.res, nrec, nb, c.cgR, c.cgP, c.rho, c.rho0, c.st);
+    cudaMemsetAsync(c.acc, 0, sizeof(double2) * nb * n, c.st);
+    // conjugate gradients on (I + lambda^-2 P_r H^{-1} H^{-H} P_r^T) z = r0; the field
+    // correction H^{-1} H^{-H} P_r^T z accumulates from the same steps
+    const double thr2 = cg_tol * cg_tol;
+    std::vector<double> rh(nb), r0h(nb);
+    bool converged = false;
+    for (int it = 0; it < cg_maxit && !converged; ++it) {
+      cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
+      launch_spread(*P, c.cgP, nrec, rec_idx, nrec, 1.0, c.ident, nb, c.q, c.st);
+      if (!solve(1, c.q, c.v)) return st;   // w = H^{-H} P_r^T p
+      if (!solve(0, c.v, c.du)) return st;  // v = H^{-1} w
+      launch_wri_ap(*P, c.du, rec_idx, nrec, inv_l2, c.cgP, c.cgAP, c.rho, c.rho0, thr2, c.alpha, nb, c.st);
+      launch_axpy_slots(c.du, c.alpha, 0.0, n, nb, c.acc, c.st);
+      launch_wri_step(nrec, nb, c.cgR, c.cgP, c.cgAP, c.alpha, c.rho, c.st);
+      cudaMemcpyAsync(rh.data(), c.rho, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.st);
+      cudaMemcpyAsync(r0h.data(), c.rho0, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.st);
+      if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+      converged = true;
+      for (int a = 0; a < nb; ++a) {
+        if (!std::isfinite(rh[a])) return HELM_E_NONFINITE;
+        if (rh[a] > thr2 * r0h[a]) converged = false;
+      }
+    }
+    for (int a = 0; a < nb; ++a)
+      if (rh[a] > thr2 * r0h[a] && r0h[a] > 0.0) rep[a].status = worst(rep[a].status, HELM_E_NOCONV);
+    // u = u0 + lambda^-2 acc; y = q - H u (FP64); f and g
+    launch_axpy_slots(c.acc, nullptr, inv_l2, n, nb, c.u, c.st);
+    sources();
+    std::vector<int> all(nb);
+    for (int a = 0; a < nb; ++a) all[a] = a;
+    set_active(c, all);
+    launch_stencil<double>(op_view<double>(c, 0, 0), c.slot_f, c.act, c.na, c.u, Scale<double>{}, c.q,
+                           Scale<double>{}, c.v, c.st);
+    launch_sqnorm(c.v, n, nb, c.partial, c.sq, c.st);
+    launch_residual_misfit(*P, c.u, rec_idx, nrec, (const double2*)d_obs, c.slot_f, c.slot_s, nsrc, c.ident, nb,
+                           c.res, c.f_slot, c.st);
+    launch_wri_f(c.f_slot, c.sq, nb, lambda * lambda, f_out, c.st);
+    // H u - q = -y:  g += lambda^2 w^2 Re(conj(u) (H u - q))
+    launch_grad_accum(c.u, nullptr, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st, -lambda * lambda);
+    for (auto& r : rep) result = worst(result, r.status);
+    fill_reports(reports, g, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
   if (const int sc = sync_check(c); sc != HELM_OK) return sc;

@@ -222,7 +222,19 @@ void launch_residual_misfit(const helm_plan& P, const double2* u, const int32_t*
 void launch_spread(const helm_plan& P, const double2* r, size_t r_stride, const int32_t* rec_idx,
                    int nrec, double sign, const int* slots, int nslots, double2* b, cudaStream_t st);
 void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
-                       const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st);
+                       const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st, double scale = 1.0);
+// WRI: receiver-space conjugate gradients (one slot per block) and helpers
+void launch_wri_init(const double2* res, int nrec, int nslots, double2* R, double2* Pd, double* rho, double* rho0,
+                     cudaStream_t st);
+void launch_wri_ap(const helm_plan& P, const double2* du, const int32_t* rec_idx, int nrec, double inv_l2,
+                   const double2* Pd, double2* AP, const double* rho, const double* rho0, double thr2, double* alpha,
+                   int nslots, cudaStream_t st);
+void launch_wri_step(int nrec, int nslots, double2* R, double2* Pd, const double2* AP, const double* alpha,
+                     double* rho, cudaStream_t st);
+void launch_axpy_slots(const double2* x, const double* c, double c0, size_t n, int nslots, double2* y,
+                       cudaStream_t st);
+void launch_sqnorm(const double2* x, size_t n, int nslots, double* part, double* sq, cudaStream_t st);
+void launch_wri_f(const double* f_slot, const double* sq, int nslots, double lam2, double* f, cudaStream_t st);
 // b_s = -w_f^2 dmc u_s for slots 0..nslots-1 (linearised state right-hand side)
 void launch_born_source(const double2* u, const double* dmc, const double* w2, const int* slot_f, int nslots,
                         size_t n, double2* b, cudaStream_t st);

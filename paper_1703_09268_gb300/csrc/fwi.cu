@@ -3,6 +3,8 @@
 // gradient (Sec. 2; Appendix A eqs. (dU2), (dH), (dHadj); Listing pdefunc).
 #include <cmath>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace helm {
@@ -230,7 +232,7 @@ __global__ void k_spread(GeomArgs g, const double2* __restrict__ r, size_t r_str
 __global__ void k_grad_accum(const double2* __restrict__ u, const int* __restrict__ u_idx,
                              const double2* __restrict__ v, const double* __restrict__ w2,
                              const int* __restrict__ slot_f, const int* __restrict__ slots, int nslots,
-                             size_t n, double* __restrict__ gcomp) {
+                             size_t n, double scale, double* __restrict__ gcomp) {
   const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double acc = gcomp[p];
@@ -238,9 +240,141 @@ __global__ void k_grad_accum(const double2* __restrict__ u, const int* __restric
     const int s = slots[a];
     const double2 uu = u[(size_t)(u_idx ? u_idx[s] : s) * n + p];
     const double2 vv = v[(size_t)s * n + p];
-    acc += w2[slot_f[s]] * (uu.x * vv.x + uu.y * vv.y);
+    acc += scale * w2[slot_f[s]] * (uu.x * vv.x + uu.y * vv.y);
   }
   gcomp[p] = acc;
+}
+
+// ---- WRI (penalty method): conjugate gradients in the receiver space ----
+// A z = r0 with A = I + lambda^-2 P_r H^{-1} H^{-H} P_r^T (Hermitian positive
+// definite), one slot per block, fixed-order reductions.
+
+__device__ __forceinline__ double block_sum_256(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// R = -(P u0 - d) = d - P u0, Pd = R, rho = rho0 = ||R||^2
+__global__ void k_wri_init(const double2* __restrict__ res, int nrec, double2* __restrict__ R,
+                           double2* __restrict__ Pd, double* __restrict__ rho, double* __restrict__ rho0) {
+  __shared__ double sh[256];
+  const int a = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+    const double2 r = res[(size_t)a * nrec + k];
+    const double2 v = make_double2(-r.x, -r.y);
+    R[(size_t)a * nrec + k] = v;
+    Pd[(size_t)a * nrec + k] = v;
+    acc += v.x * v.x + v.y * v.y;
+  }
+  const double t = block_sum_256(acc, sh);
+  if (threadIdx.x == 0) {
+    rho[a] = t;
+    rho0[a] = t;
+  }
+}
+
+// AP = Pd + lambda^-2 P_r du;  alpha = rho / Re<Pd, AP> (0 once the slot has converged)
+__global__ void k_wri_ap(GeomArgs g, const double2* __restrict__ du, size_t n, const int32_t* __restrict__ rec_idx,
+                         int nrec, double inv_l2, const double2* __restrict__ Pd, double2* __restrict__ AP,
+                         const double* __restrict__ rho, const double* __restrict__ rho0, double thr2,
+                         double* __restrict__ alpha) {
+  __shared__ double sh[256];
+  const int a = blockIdx.x;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+    size_t c;
+    double2 v = make_double2(0, 0);
+    if (phys_to_comp(g, rec_idx[k], &c)) v = du[(size_t)a * n + c];
+    const double2 pk = Pd[(size_t)a * nrec + k];
+    const double2 ap = make_double2(pk.x + inv_l2 * v.x, pk.y + inv_l2 * v.y);
+    AP[(size_t)a * nrec + k] = ap;
+    acc += pk.x * ap.x + pk.y * ap.y;
+  }
+  const double pap = block_sum_256(acc, sh);
+  if (threadIdx.x == 0) {
+    const bool live = rho[a] > thr2 * rho0[a] && pap > 0.0 && isfinite(pap);
+    alpha[a] = live ? rho[a] / pap : 0.0;
+  }
+}
+
+// R -= alpha AP;  rho' = ||R||^2;  Pd = R + (rho'/rho) Pd;  rho = rho'
+__global__ void k_wri_step(int nrec, double2* __restrict__ R, double2* __restrict__ Pd,
+                           const double2* __restrict__ AP, const double* __restrict__ alpha,
+                           double* __restrict__ rho) {
+  __shared__ double sh[256];
+  const int a = blockIdx.x;
+  const double al = alpha[a];
+  if (al == 0.0) return;  // converged slot: the whole block leaves together
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+    double2 r = R[(size_t)a * nrec + k];
+    const double2 ap = AP[(size_t)a * nrec + k];
+    r.x -= al * ap.x;
+    r.y -= al * ap.y;
+    R[(size_t)a * nrec + k] = r;
+    acc += r.x * r.x + r.y * r.y;
+  }
+  const double rn = block_sum_256(acc, sh);
+  const double beta = rho[a] > 0.0 ? rn / rho[a] : 0.0;
+  for (int k = threadIdx.x; k < nrec; k += blockDim.x) {
+    const double2 r = R[(size_t)a * nrec + k];
+    const double2 pk = Pd[(size_t)a * nrec + k];
+    Pd[(size_t)a * nrec + k] = make_double2(r.x + beta * pk.x, r.y + beta * pk.y);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) rho[a] = rn;
+}
+
+// y_s += c_s x_s for slots 0..nslots-1 (c per slot, or the constant c0 when c is null)
+__global__ void k_axpy_slots(const double2* __restrict__ x, const double* __restrict__ c, double c0, size_t n,
+                             double2* __restrict__ y) {
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int a = blockIdx.y;
+  const double w = c ? c[a] : c0;
+  if (w == 0.0) return;
+  const double2 v = x[(size_t)a * n + p];
+  double2 t = y[(size_t)a * n + p];
+  t.x = fma(w, v.x, t.x);
+  t.y = fma(w, v.y, t.y);
+  y[(size_t)a * n + p] = t;
+}
+
+// sq[a] = ||x_a||^2: per-block partial sums, then one block per slot adds them in order
+__global__ void k_sqnorm_partial(const double2* __restrict__ x, size_t n, int nblk, double* __restrict__ part) {
+  __shared__ double sh[256];
+  const int a = blockIdx.y;
+  double acc = 0.0;
+  for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)nblk * blockDim.x) {
+    const double2 v = x[(size_t)a * n + p];
+    acc += v.x * v.x + v.y * v.y;
+  }
+  const double t = block_sum_256(acc, sh);
+  if (threadIdx.x == 0) part[(size_t)a * nblk + blockIdx.x] = t;
+}
+__global__ void k_sqnorm_fold(const double* __restrict__ part, int nblk, int nslots, double* __restrict__ sq) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nslots) return;
+  double t = 0.0;
+  for (int b = 0; b < nblk; ++b) t += part[(size_t)a * nblk + b];
+  sq[a] = t;
+}
+
+// f += sum_a f_slot[a] + lam2/2 sum_a sq[a]  (slots in order)
+__global__ void k_wri_f(const double* __restrict__ f_slot, const double* __restrict__ sq, int nslots, double lam2,
+                        double* __restrict__ f) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = f[0];
+  for (int a = 0; a < nslots; ++a) t += f_slot[a] + 0.5 * lam2 * sq[a];
+  f[0] = t;
 }
 
 // Right-hand side of the linearised state equation (Appendix A, eq. (dU2)
@@ -438,10 +572,55 @@ void launch_spread(const helm_plan& P, const double2* r, size_t r_stride, const 
 }
 
 void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
-                       const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st) {
+                       const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st, double scale) {
   if (nslots <= 0) return;
   ProfScope ps(PC_FWI, (double)nslots * n * 2 * sizeof(double2) + (double)n * 2 * sizeof(double), st);
-  k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n, gcomp);
+  k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n, scale,
+                                                            gcomp);
+  count_launch();
+}
+
+void launch_wri_init(const double2* res, int nrec, int nslots, double2* R, double2* Pd, double* rho, double* rho0,
+                     cudaStream_t st) {
+  if (nslots <= 0) return;
+  k_wri_init<<<nslots, 256, 0, st>>>(res, nrec, R, Pd, rho, rho0);
+  count_launch();
+}
+
+void launch_wri_ap(const helm_plan& P, const double2* du, const int32_t* rec_idx, int nrec, double inv_l2,
+                   const double2* Pd, double2* AP, const double* rho, const double* rho0, double thr2, double* alpha,
+                   int nslots, cudaStream_t st) {
+  if (nslots <= 0) return;
+  k_wri_ap<<<nslots, 256, 0, st>>>(geom(P), du, P.lev[0].n, rec_idx, nrec, inv_l2, Pd, AP, rho, rho0, thr2, alpha);
+  count_launch();
+}
+
+void launch_wri_step(int nrec, int nslots, double2* R, double2* Pd, const double2* AP, const double* alpha,
+                     double* rho, cudaStream_t st) {
+  if (nslots <= 0) return;
+  k_wri_step<<<nslots, 256, 0, st>>>(nrec, R, Pd, AP, alpha, rho);
+  count_launch();
+}
+
+void launch_axpy_slots(const double2* x, const double* c, double c0, size_t n, int nslots, double2* y,
+                       cudaStream_t st) {
+  if (nslots <= 0) return;
+  dim3 grd((unsigned)((n + 255) / 256), nslots);
+  k_axpy_slots<<<grd, 256, 0, st>>>(x, c, c0, n, y);
+  count_launch();
+}
+
+void launch_sqnorm(const double2* x, size_t n, int nslots, double* part, double* sq, cudaStream_t st) {
+  if (nslots <= 0) return;
+  const int nblk = (int)std::max<size_t>(1, std::min<size_t>(32, (n + 255) / 256));
+  dim3 grd(nblk, nslots);
+  k_sqnorm_partial<<<grd, 256, 0, st>>>(x, n, nblk, part);
+  k_sqnorm_fold<<<(nslots + 127) / 128, 128, 0, st>>>(part, nblk, nslots, sq);
+  count_launch(2);
+}
+
+void launch_wri_f(const double* f_slot, const double* sq, int nslots, double lam2, double* f, cudaStream_t st) {
+  k_wri_f<<<1, 32, 0, st>>>(f_slot, sq, nslots, lam2, f);
   count_launch();
 }
 

@@ -135,7 +135,7 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   C.q = bp.take<double2>((size_t)B * n0);
   C.u = bp.take<double2>((size_t)B * n0);
   const bool born = call == HELM_CALL_BORN || call == HELM_CALL_BORN_ADJOINT || call == HELM_CALL_GN_HESSVEC ||
-                    call == HELM_CALL_HESSVEC || call == HELM_CALL_MISFIT_GRAD_25D;
+                    call == HELM_CALL_HESSVEC || call == HELM_CALL_MISFIT_GRAD_25D || call == HELM_CALL_WRI;
   if (call == HELM_CALL_ADJOINT || call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT || born)
     C.v = bp.take<double2>((size_t)B * n0);
   C.nrm = bp.take<double>(B);
@@ -154,13 +154,25 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
     C.wav = bp.take<double2>(nfreq);
   }
   if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_MISFIT || call == HELM_CALL_HESSVEC ||
-      call == HELM_CALL_MISFIT_GRAD_25D) {
+      call == HELM_CALL_MISFIT_GRAD_25D || call == HELM_CALL_WRI) {
     C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
     C.f_slot = bp.take<double>(B);
   }
-  if (call == HELM_CALL_HESSVEC) C.du = bp.take<double2>((size_t)B * n0);
+  if (call == HELM_CALL_HESSVEC || call == HELM_CALL_WRI) C.du = bp.take<double2>((size_t)B * n0);
+  if (call == HELM_CALL_WRI) {
+    const size_t nr = (size_t)B * (nrec > 0 ? nrec : 1);
+    C.acc = bp.take<double2>((size_t)B * n0);
+    C.cgR = bp.take<double2>(nr);
+    C.cgP = bp.take<double2>(nr);
+    C.cgAP = bp.take<double2>(nr);
+    C.rho = bp.take<double>(B);
+    C.rho0 = bp.take<double>(B);
+    C.alpha = bp.take<double>(B);
+    C.sq = bp.take<double>(B);
+  }
   if (call == HELM_CALL_MISFIT_GRAD || call == HELM_CALL_GRADIENT || call == HELM_CALL_BORN_ADJOINT ||
-      call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC || call == HELM_CALL_MISFIT_GRAD_25D)
+      call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC || call == HELM_CALL_MISFIT_GRAD_25D ||
+      call == HELM_CALL_WRI)
     C.gcomp = bp.take<double>(n0);
   if (call == HELM_CALL_GN_HESSVEC) C.res = bp.take<double2>((size_t)B * (nrec > 0 ? nrec : 1));
   if (call == HELM_CALL_BORN || call == HELM_CALL_GN_HESSVEC || call == HELM_CALL_HESSVEC)

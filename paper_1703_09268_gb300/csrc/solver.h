@@ -80,6 +80,15 @@ struct Ctx {
   double* shift = nullptr; // [nfreq] diagonal shift per (virtual) frequency (2.5D: k_y^2), or null
   double* ck = nullptr;    // [nfreq] 2.5D quadrature weight per virtual frequency
   double2* wav = nullptr;  // [nfreq] 2.5D wavelet per virtual frequency
+  // WRI: field accumulator and receiver-space conjugate-gradient state
+  double2* acc = nullptr;  // [B][n]
+  double2* cgR = nullptr;  // [B][nrec] residual
+  double2* cgP = nullptr;  // [B][nrec] search direction
+  double2* cgAP = nullptr; // [B][nrec] A times the direction
+  double* rho = nullptr;   // [B] ||R||^2
+  double* rho0 = nullptr;  // [B] initial ||R||^2
+  double* alpha = nullptr; // [B] step length
+  double* sq = nullptr;    // [B] ||H u - q||^2
   // Krylov hierarchies
   Hierarchy<float> h32;
   Hierarchy<double> h64;

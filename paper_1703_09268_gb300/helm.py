@@ -23,7 +23,7 @@ FP64, MIXED = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
 CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT, CALL_PRECOND = \
     0, 1, 2, 3, 4, 5, 6
-CALL_BORN, CALL_BORN_ADJOINT, CALL_GN_HESSVEC, CALL_HESSVEC, CALL_MISFIT_GRAD_25D = 7, 8, 9, 10, 11
+CALL_BORN, CALL_BORN_ADJOINT, CALL_GN_HESSVEC, CALL_HESSVEC, CALL_MISFIT_GRAD_25D, CALL_WRI = 7, 8, 9, 10, 11, 12
 PROF_CLASSES = ["stencil_c64", "stencil_c128", "krylov_c64", "krylov_c128", "small", "transfer", "fwi",
                 "misc", "stencil_c64_coarse", "krylov_c64_coarse", "gram_c64", "update_c64"]
 
@@ -61,7 +61,7 @@ class HelmBatchItem(ctypes.Structure):
 EXPORTS = ["helm_default_opts", "helm_misfit_and_gradient_batch", "helm_plan_create", "helm_plan_destroy", "helm_plan_dims",
            "helm_workspace_size", "helm_apply", "helm_precond_apply", "helm_forward", "helm_adjoint", "misfit_and_gradient",
            "helm_misfit", "helm_gradient", "helm_born", "helm_born_adjoint", "helm_gn_hessvec", "helm_hessvec",
-           "helm_misfit_and_gradient_25d",
+           "helm_misfit_and_gradient_25d", "helm_wri_misfit_and_gradient",
            "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read",
            "helm_check_bounded_wait"]
 
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(HelmRhsReport), P]
     lib.helm_misfit_and_gradient_25d.argtypes = [P, P, ctypes.POINTER(D), I, ctypes.POINTER(D), ctypes.POINTER(D), I,
                                                  P, I, P, I, P, P, I, P, P, P, P, S, ctypes.POINTER(HelmRhsReport), P]
+    lib.helm_wri_misfit_and_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, D, D, I, P, P, P,
+                                                 S, ctypes.POINTER(HelmRhsReport), P]
     lib.helm_misfit.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, P, S,
                                 ctypes.POINTER(HelmRhsReport), P]
     lib.helm_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, P, P, S,
@@ -486,6 +488,34 @@ def misfit_and_gradient_25d(plan: Plan, m_phys, freqs_hz, ky, ck, src_idx, Q, re
                                               _ptr(rec_idx), nrec, _ptr(d_obs), _ptr(f), _ptr(g), ws, nb, rep,
                                               _stream(dev))
     _check(code, "helm_misfit_and_gradient_25d", allow_noconv=True)
+    return f, g, reports_to_list(rep)
+
+
+def wri_misfit_and_gradient(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, lam, cg_tol=1e-10,
+                            cg_maxit=200, wavelet=None):
+    """WRI (penalty) objective and gradient; the field of every pair comes from
+    receiver-space conjugate gradients.  Returns (f [1], g [n_phys], reports)."""
+    _dev(m_phys, torch.float64, "m_phys")
+    _dev(src_idx, torch.int32, "src_idx")
+    _dev(Q, torch.complex128, "Q")
+    _dev(rec_idx, torch.int32, "rec_idx")
+    _dev(d_obs, torch.complex128, "d_obs")
+    if wavelet is not None:
+        _dev(wavelet, torch.complex128, "wavelet")
+    nfreq = len(np.atleast_1d(freqs_hz))
+    _check_common(plan, m_phys, src_idx, Q, wavelet, nfreq)
+    nsrc, nrec = Q.shape[1], rec_idx.numel()
+    _need(tuple(d_obs.shape) == (nfreq, nsrc, nrec), "d_obs must be [nfreq, nsrc, nrec]")
+    dev = m_phys.device
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(plan.n_phys, dtype=torch.float64, device=dev)
+    rep = _reports(nfreq * nsrc)
+    ws, nb = plan.workspace(plan.workspace_size(CALL_WRI, nfreq, nsrc, nrec))
+    code = lib().helm_wri_misfit_and_gradient(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx),
+                                              src_idx.numel(), _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec,
+                                              _ptr(d_obs), float(lam), float(cg_tol), int(cg_maxit), _ptr(f), _ptr(g),
+                                              ws, nb, rep, _stream(dev))
+    _check(code, "helm_wri_misfit_and_gradient", allow_noconv=True)
     return f, g, reports_to_list(rep)
 
 

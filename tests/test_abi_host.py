@@ -127,8 +127,10 @@ def test_workspace_sizes_of_the_other_calls(helm):
     w1 = p2.workspace_size(helm.CALL_MISFIT_GRAD_25D, 4, 3, 11)
     w2 = p2.workspace_size(helm.CALL_MISFIT_GRAD_25D, 8, 3, 11)
     assert 0 < w1 < w2
+    # WRI keeps the field accumulator and the receiver-space CG state besides the gradient's fields
+    assert p.workspace_size(helm.CALL_WRI, 1, 8, 16) > m
     with pytest.raises(helm.HelmError):
-        p.workspace_size(helm.CALL_MISFIT_GRAD_25D + 1, 1, 1, 1)
+        p.workspace_size(helm.CALL_WRI + 1, 1, 1, 1)
 
 
 def test_new_calls_reject_bad_arguments_before_any_device_work(helm):
@@ -161,3 +163,9 @@ def test_new_calls_reject_bad_arguments_before_any_device_work(helm):
     assert L.helm_misfit_and_gradient_25d(p2._h, fake, fr, 1, ky, ck, 0, *args) == helm.HELM_E_INVAL
     bad = (ctypes.c_double * 2)(0.01, float("nan"))
     assert L.helm_misfit_and_gradient_25d(p2._h, fake, fr, 1, bad, ck, 2, *args) == helm.HELM_E_INVAL
+    # WRI needs lambda > 0, cg_tol > 0 and at least one CG iteration
+    wargs = (fake, 1, fake, 1, None, fake, 1, fake)
+    tail = (fake, fake, fake, 1 << 20, rep, None)
+    assert L.helm_wri_misfit_and_gradient(p3._h, fake, fr, 1, *wargs, 0.0, 1e-10, 10, *tail) == helm.HELM_E_INVAL
+    assert L.helm_wri_misfit_and_gradient(p3._h, fake, fr, 1, *wargs, 1e3, 0.0, 10, *tail) == helm.HELM_E_INVAL
+    assert L.helm_wri_misfit_and_gradient(p3._h, fake, fr, 1, *wargs, 1e3, 1e-10, 0, *tail) == helm.HELM_E_INVAL
