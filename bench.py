@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--op", default="misfit_grad", choices=["misfit_grad", "gn", "hess"],
                    help="step mode: misfit + gradient, the Gauss-Newton product J^T J dm, or the full Hessian product")
     p.add_argument("--nk", type=int, default=16, help="2.5D mode: k_y quadrature nodes")
-    p.add_argument("--mode", default="step", choices=["step", "apply", "batch", "25d"],
+    p.add_argument("--lam", type=float, default=1e4, help="WRI mode: penalty weight lambda")
+    p.add_argument("--mode", default="step", choices=["step", "apply", "batch", "25d", "wri"],
                    help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
                         "workload's 16 complex64 fields)")
     return p.parse_args()
@@ -370,6 +371,56 @@ def run_25d(args):
     print(json.dumps(out), flush=True)
 
 
+def run_wri(args):
+    """WRI (penalty) objective + gradient on the 401 x 201 x-z section of the
+    2.5D workload (as a 2D problem): per pair one state solve plus two solves per
+    receiver-space CG iteration."""
+    import torch
+    from paper_1703_09268_gb300 import helm, synth
+
+    dev = torch.device("cuda", 0)
+    wl = synth.workload_25d()
+    grid = helm.make_grid(2, wl.n, wl.h, wl.npml, wl.v_ref, levels=2)
+    kso, ksi, kco, kci = (int(v) for v in args.smoother.split(","))
+    plan = helm.Plan(grid, helm.default_opts(
+        precision=helm.MIXED if args.precision == "mixed" else helm.FP64, precond=helm.PRECOND_MLGMRES,
+        k_inner=args.k_inner or 10, tol=args.tol, max_cycles=400, tol_inner=args.tol_inner, k_so=kso, k_si=ksi,
+        k_co=kco, k_ci=kci, max_batch=args.max_batch), device=dev)
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    m0 = T(wl.m0.ravel(), torch.float64)
+    src, Q, rec = T(wl.src_idx, torch.int32), T(wl.Q, torch.complex128), T(wl.rec_idx, torch.int32)
+    # observed data: the 2D field of the true model at the receivers (input generation, untimed)
+    p64 = helm.Plan(grid, helm.default_opts(precision=helm.FP64, precond=helm.PRECOND_MLGMRES, tol=1e-12,
+                                            max_cycles=400), device=dev)
+    _, d_obs, _ = helm.helm_forward(p64, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
+                                    want_fields=False)
+    step = lambda: helm.wri_misfit_and_gradient(plan, m0, wl.freqs_hz, src, Q, rec, d_obs, args.lam,  # noqa: E731
+                                                cg_tol=1e-8, cg_maxit=100)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f, g, rep = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    units = wl.nsrc * wl.nfreq
+    out = dict(mode="wri", metric="WRI misfit+gradient (src\u00b7freq)/s", value=round(units / (ms / 1e3), 3),
+               unit=UNIT, ms_per_step=round(ms, 3), steps=args.steps, warmup=args.warmup, n_gpus=1,
+               config=dict(workload=wl.name.replace("2.5d", "2d"), grid_comp=list(plan.N), lam=args.lam,
+                           cg_tol=1e-8, sources=wl.nsrc, receivers=wl.nrec),
+               solver=dict(solver_iters_per_pair=float(np.mean([r["iters"] for r in rep])),
+                           statuses=sorted({r["status"] for r in rep})),
+               f=float(f.item()))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -380,6 +431,8 @@ def main():
         return run_batch(args)
     if args.mode == "25d":
         return run_25d(args)
+    if args.mode == "wri":
+        return run_wri(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
