@@ -370,20 +370,21 @@ int helm_misfit_and_gradient_batch(helm_batch_item* items, int nitems, int nwork
 
 /* helm_apply without a workspace argument (the paper has no counterpart: this
  * is an interface convenience).  For callers that cannot allocate device
- * memory where they apply the operator -- code running during CUDA stream
- * capture (cudaMalloc is not allowed there), hosts whose framework owns every
- * device allocation, serving loops that must not allocate per request.  The
- * scratch helm_apply takes from its workspace (extended model, damping
- * tables, slot lists) lives instead in one static device array of
- * HELM_NOALLOC_SCRATCH_BYTES inside the library, present on every GPU that
- * loads the library until the process exits.  Enough for fields of up to
- * about 1.3 million computational nodes; larger problems return
- * HELM_E_NOMEM (use helm_apply with a workspace).  The first call on a device
- * looks up the array's device address with that device current; make it
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents: calls whose GPU work overlaps (other streams or host
- * threads) race and must be serialised.  The call allocates nothing.
- * Arguments and results are those of helm_apply. */
+ * memory where they apply the operator: hosts whose framework owns every
+ * device allocation through its own pool and forbids raw cudaMalloc, and
+ * serving loops that must not allocate per request.  The scratch helm_apply
+ * takes from its workspace (extended model, damping tables, slot lists)
+ * lives instead in one static device array of HELM_NOALLOC_SCRATCH_BYTES
+ * inside the library, present on every GPU that loads the library until the
+ * process exits.  Enough for fields of up to about 1.3 million computational
+ * nodes; larger problems return HELM_E_NOMEM (use helm_apply with a
+ * workspace).  The first call on a device looks up the array's device address
+ * with that device current.  Like helm_apply, the call copies small host
+ * arrays to the device and synchronises `stream` before it returns, so it
+ * cannot be recorded into a CUDA graph by stream capture.  All calls share
+ * the array and it keeps the last call's contents: calls whose GPU work
+ * overlaps (other streams or host threads) race and must be serialised.  The
+ * call allocates nothing.  Arguments and results are those of helm_apply. */
 #define HELM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int helm_apply_noalloc(helm_plan* plan, const double* m_phys, double freq_hz, int adjoint,
                        int precision, const void* x, void* y, int nrhs, helm_stream_t stream);

@@ -5,12 +5,13 @@
 // FP32 copies), the damping-layer coefficient tables and the per-field slot
 // lists; normally the caller allocates it and passes it in.  Some callers
 // cannot allocate device memory at the point where they apply the operator:
-// code that runs while a CUDA stream is being captured into a graph (where
-// cudaMalloc is not permitted), code embedded in a host framework that owns
-// every device allocation through its own pool and forbids raw cudaMalloc,
-// and latency-critical serving loops that must not allocate per request.
-// For them this file keeps the scratch in one file-scope device array of
-// fixed size, so a call allocates nothing.
+// code embedded in a host framework that owns every device allocation
+// through its own pool and forbids raw cudaMalloc, and latency-critical
+// serving loops that must not allocate per request.  For them this file
+// keeps the scratch in one file-scope device array of fixed size, so a call
+// allocates nothing.  The call is not meant for stream capture: like
+// helm_apply it copies small host arrays to the device and synchronises its
+// stream before returning.
 //
 // The array lives in every GPU that loads the library, until the process
 // exits.  Every call shares it, and it keeps whatever the last call wrote, so

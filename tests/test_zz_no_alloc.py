@@ -1,9 +1,9 @@
 """helm_apply_noalloc against helm_apply, through the C ABI.
 
 helm_apply_noalloc exists for callers that cannot allocate device memory where
-they apply the operator (inside CUDA stream capture, under a framework that
-owns every allocation, in per-request serving loops); it keeps its scratch in
-a static device array instead of a caller workspace.  This test calls it twice
+they apply the operator (under a framework that owns every allocation, in
+per-request serving loops); it keeps its scratch in a static device array
+instead of a caller workspace.  This test calls it twice
 in a row (the second call reuses the array the first one left behind) and
 compares each result with the workspace entry point, within the operator
 tolerances of the parity tests.  It runs last so that a failure here comes
