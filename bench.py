@@ -1,17 +1,24 @@
 #!/usr/bin/env python
 """Benchmark: frequency-domain FWI misfit + adjoint-state gradient throughput.
 
-One step = f and g = E^T sum_s w^2 Re(conj(u_s) v_s) over every (source,
-frequency) pair of the workload: 2 batched Helmholtz solves per pair (forward
-and adjoint), complex64 FGMRES + ML-GMRES inner solves inside FP64 iterative
-refinement, receiver restriction, adjoint sources and gradient accumulation,
-all in libhelm.so's kernels.
+One step = f and g = E^T sum w^2 Re(conj(u) v) over a fixed set of (source,
+frequency) pairs: 2 batched Helmholtz solves per pair (forward and adjoint),
+complex64 FGMRES + ML-GMRES inner solves inside FP64 iterative refinement,
+receiver restriction, adjoint sources and gradient accumulation, all in
+libhelm.so's kernels.
 
-Workload (N=1): 64^3 physical grid, h = 25 m, 10-cell damping layer, seeded
-layered velocity 1500-4500 m/s smoothed (sigma 2 cells), 4 Hz, 16 point
-sources on a 4x4 grid at z = 50 m, receivers at every surface node.  With N
-ranks (torchrun) every rank evaluates its own 16 sources and the ranks sum f
-and g with one all-reduce (the paper's sum over workers): weak scaling.
+Default workload (N=1): the multi-frequency differentiation model -- 192^3
+physical grid, h = 25 m, 10-cell damping layers (213^3 computational nodes),
+seeded layered velocity 1500-4500 m/s with 20 Gaussian inclusions as the true
+model and its smoothed version as the evaluation model, 128 sources on an 8x16
+surface grid, receivers at every surface node, 8 frequencies 2-8 Hz.  A step
+evaluates one source (the one nearest the centre) at all 8 frequencies: 8 of
+the workload's 1024 pairs, each solve on the full grid.  With N ranks
+(torchrun) rank r takes the next source along, and the ranks sum f and g with
+one all-reduce (the paper's sum over workers): weak scaling.
+
+`--workload layered64` selects the smaller 64^3 layered model (4 Hz, 16
+sources per step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -51,11 +58,19 @@ def parse():
     p.add_argument("--k-inner", type=int, default=0, help="outer FGMRES cycle length (0: 10 with ML-GMRES, else 30)")
     p.add_argument("--reorth", type=int, default=1)
     p.add_argument("--max-batch", type=int, default=0, help="right-hand sides solved together (0 = all)")
-    p.add_argument("--smoother", default="3,6,3,6", help="ML-GMRES (k_so, k_si, k_co, k_ci)")
-    p.add_argument("--n", type=int, default=64)
+    p.add_argument("--smoother", default=None, help="ML-GMRES (k_so, k_si, k_co, k_ci); default 3,6,8,6 on "
+                   "multifreq192, 3,6,3,6 on layered64")
+    p.add_argument("--workload", default="multifreq192", choices=["multifreq192", "layered64"])
+    p.add_argument("--step-sources", type=int, default=1,
+                   help="multifreq192: sources per step (each at all 8 frequencies)")
+    p.add_argument("--n", type=int, default=64, help="layered64: grid size")
+    p.add_argument("--e2e-steps", type=int, default=3, help="steps timed end to end from host buffers")
+    p.add_argument("--fp64-calls", type=int, default=5, help="timed calls of the FP64 per-source baseline")
+    p.add_argument("--no-accuracy", action="store_true")
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-seconds", type=float, default=None,
+                   help="oracle sample per process (default 20 s on the 192^3 model, 15 s on the 64^3 one)")
     p.add_argument("--workers", type=int, default=4, help="batch mode: models in flight together")
     p.add_argument("--op", default="misfit_grad", choices=["misfit_grad", "gn", "hess"],
                    help="step mode: misfit + gradient, the Gauss-Newton product J^T J dm, or the full Hessian product")
@@ -64,23 +79,29 @@ def parse():
     p.add_argument("--mode", default="step", choices=["step", "apply", "batch", "25d", "wri"],
                    help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
                         "workload's 16 complex64 fields)")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.cpu_seconds is None:
+        a.cpu_seconds = 20.0 if a.workload == "multifreq192" else 15.0
+    if a.smoother is None:
+        a.smoother = "3,6,8,6" if a.mode == "step" and a.workload == "multifreq192" else "3,6,3,6"
+    return a
 
 
 def run_apply(args):
-    """Stencil microbenchmark: y = H x for the workload's 16 fields, complex64 and complex128."""
+    """Stencil microbenchmark: y = H x for the workload's step fields (192^3 model: 8 fields of 213^3;
+    64^3 model: 16 fields of 85^3), complex64 with every tile shape and the tuned one, and complex128."""
     import torch
     from paper_1703_09268_gb300 import helm
     dev = torch.device("cuda", 0)
-    wl = workload(args.n, 0, 1)
+    wl, name = make_workload(args, 0, 1)
+    nf = wl.nsrc * wl.nfreq
     plan = helm.Plan(helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=args.levels), helm.default_opts(),
                      device=dev)
     m0 = torch.as_tensor(wl.m0.ravel(), dtype=torch.float64, device=dev)
     hbm, kind = peaks()
-    out = dict(mode="apply", workload=wl.name, grid_comp=list(plan.N), fields=wl.nsrc)
-    for name, dt, bpp in (("c64", torch.complex64, 16.0), ("c128", torch.complex128, 32.0)):
-        x = torch.randn(wl.nsrc, plan.n_comp, dtype=dt, device=dev)
-        y = torch.empty_like(x)
+    out = dict(mode="apply", workload=name, grid_comp=list(plan.N), fields=nf, peak=hbm, peak_kind=kind)
+
+    def timed(x, y):
         for _ in range(args.warmup):
             helm.helm_apply(plan, m0, wl.freqs_hz[0], x, out=y)
         helm.profile_enable(True)
@@ -88,11 +109,24 @@ def run_apply(args):
             helm.helm_apply(plan, m0, wl.freqs_hz[0], x, out=y)
         prof = helm.profile_read()
         helm.profile_enable(False)
-        st = prof["stencil_" + name]
-        t = st["ms"] / 1e3
-        out[name] = dict(gpts=round(st["bytes"] / bpp / t / 1e9, 1), gbs=round(st["bytes"] / t / 1e9, 1),
-                         frac=round(st["bytes"] / t / 1e9 / hbm, 3), us_per_launch=round(1e6 * t / st["launches"], 2),
-                         peak=hbm, peak_kind=kind)
+        return prof
+
+    for name_, dt, bpp in (("c64", torch.complex64, 16.0), ("c128", torch.complex128, 32.0)):
+        x = torch.randn(nf, plan.n_comp, dtype=dt, device=dev)
+        y = torch.empty_like(x)
+        shapes = ([(v, sh) for v, sh in enumerate(helm.stencil_variants())] if name_ == "c64" else []) + [(-1, None)]
+        for v, sh in shapes:
+            helm.stencil_select(v)
+            st = timed(x, y)["stencil_" + name_]
+            t = st["ms"] / 1e3
+            rec = dict(gpts=round(st["bytes"] / bpp / t / 1e9, 1), gbs=round(st["bytes"] / t / 1e9, 1),
+                       frac=round(st["bytes"] / t / 1e9 / hbm, 3), us_per_launch=round(1e6 * t / st["launches"], 2))
+            if v >= 0:
+                out.setdefault("c64_shapes", []).append(dict(shape=sh, **rec))
+            else:
+                tuned = helm.stencil_tuned(plan, 0)
+                out[name_] = dict(rec, tuned_shape=tuned[0] if tuned and name_ == "c64" else None)
+        helm.stencil_select(-1)
     print(json.dumps(out), flush=True)
 
 
@@ -146,7 +180,7 @@ def peaks():
 
 
 def workload(n, rank, world):
-    """16 sources per rank on a (4*world) x 4 surface grid; rank r takes every world-th."""
+    """64^3 layered model: 16 sources per rank on a (4*world) x 4 surface grid; rank r takes every world-th."""
     from paper_1703_09268_gb300 import synth
     wl = synth.workload_3d_layered(n=n, h=25.0 * 64 / n)
     if world > 1:
@@ -157,32 +191,33 @@ def workload(n, rank, world):
     return wl
 
 
-# ---------------------------------------------------------------------------
-# CPU baseline: the oracle's restarted GMRES on the same operator
-# ---------------------------------------------------------------------------
-
-def _oracle_worker(args):
-    n, seconds, seed = args
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    sys.path.insert(0, ROOT)
-    import numpy as _np
-    from oracle import helmholtz as O
+def step_columns(wl, rank, k):
+    """Source columns of rank r's step: k consecutive sources starting after the
+    centre source's r*k predecessors (the centre source first on rank 0)."""
     from paper_1703_09268_gb300 import synth
-    wl = synth.workload_3d_layered(n=n, h=25.0 * 64 / n)
-    g = O.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=2)
-    t0 = time.time()
-    H = O.helmholtz_matrix(g, O.extend(g, wl.m0), 2 * _np.pi * wl.freqs_hz[0])
-    q = O.source_fields(g, wl.src_idx, wl.Q)[seed % wl.nsrc]
-    t_setup = time.time() - t0
-    # bounded sample: GMRES(60) cycles until the time budget is spent
-    it_total, t_run = 0, 0.0
-    x = None
-    while t_run < seconds:
-        t1 = time.time()
-        x, it, _ = O.gmres(H, q, tol=1e-30, restart=60, maxiter=60, x0=x)
-        t_run += time.time() - t1
-        it_total += it
-    return dict(iters=it_total, seconds=t_run, setup=t_setup)
+    s0 = synth.centre_source(wl)
+    return [(s0 + rank * k + i) % wl.nsrc for i in range(k)]
+
+
+def workload_multifreq(rank, world, k):
+    """192^3 x 128 sources x 8 frequencies; the step's sources of this rank, all frequencies."""
+    from paper_1703_09268_gb300 import synth
+    wl = synth.workload_3d_multifreq()
+    cols = step_columns(wl, rank, k)
+    wl.meta["columns"] = cols
+    wl.meta["nsrc_total"] = wl.nsrc
+    wl.src_idx, wl.Q = synth.source_subset(wl, cols)
+    return wl
+
+
+def make_workload(args, rank, world):
+    if args.workload == "multifreq192":
+        wl = workload_multifreq(rank, world, args.step_sources)
+        name = (f"{wl.name}: step = {wl.nsrc} source(s) x {wl.nfreq} frequencies "
+                f"({wl.nsrc * wl.nfreq} of {wl.meta['nsrc_total'] * wl.nfreq} pairs)")
+        return wl, name
+    wl = workload(args.n, rank, world)
+    return wl, wl.name
 
 
 # DRAM traffic of the single-precision stencil from one ncu capture
@@ -201,41 +236,145 @@ def stencil_traffic(kernel_class, bytes_per_launch):
     return round(t["dram_bytes"] * bytes_per_launch / t["algorithmic_bytes"], 1)
 
 
-def cpu_baseline(n, seconds):
-    """(src.freq)/s of the oracle on the host cores: a bounded sample of GMRES
-    iterations on the full-size operator in one spawned process per core,
-    scaled by the oracle's own iteration count for a forward + adjoint solve."""
-    import multiprocessing as mp
-    path = os.path.join(ROOT, "oracle", "data", f"gmres_iterations_3d_layered_{n}.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as fh:
-        iters = json.load(fh)
-    per_pair_iters = iters["forward_iterations"] + iters["adjoint_iterations"]
-    procs = max(1, min(os.cpu_count() or 1, 16))
-    ctx = mp.get_context("spawn")
-    # one BLAS thread per spawned process (set before the children import numpy)
-    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in saved:
-        os.environ[k] = "1"
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle's restarted GMRES on the same operator
+# ---------------------------------------------------------------------------
+
+def _host_mem_gb():
     try:
-        with ctx.Pool(procs) as pool:
-            res = pool.map(_oracle_worker, [(n, seconds, i) for i in range(procs)])
+        with open("/proc/meminfo") as fh:
+            for line in fh:
+                if line.startswith("MemAvailable:"):
+                    return float(line.split()[1]) / 1e6
+    except OSError:
+        pass
+    return None
+
+
+def _oracle_setup(spec):
+    """Operator, right-hand side of one pair of the workload `spec` (oracle only)."""
+    import numpy as _np
+    from oracle import helmholtz as O
+    from paper_1703_09268_gb300 import synth
+    if spec["kind"] == "multifreq192":
+        wl = synth.workload_3d_multifreq()
+        src, Q = synth.source_subset(wl, [synth.centre_source(wl)])
+        fr = wl.freqs_hz[spec["k"] % wl.nfreq]
+    else:
+        wl = synth.workload_3d_layered(n=spec["n"], h=25.0 * 64 / spec["n"])
+        src, Q = wl.src_idx, wl.Q[:, spec["k"] % wl.nsrc:spec["k"] % wl.nsrc + 1]
+        fr = wl.freqs_hz[0]
+    g = O.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=2)
+    H = O.helmholtz_matrix(g, O.extend(g, wl.m0), 2 * _np.pi * fr)
+    q = O.source_fields(g, src, Q)[0]
+    return O, H, q, list(g.N)
+
+
+_ORACLE = {}
+
+
+def _oracle_init(kind, n):
+    """Pool initializer: build this process's operator and right-hand side once
+    (process i takes frequency / source i of the workload)."""
+    import multiprocessing as _mp
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    ident = _mp.current_process()._identity
+    k = (ident[0] - 1) if ident else 0
+    t0 = time.time()
+    O, H, q, N = _oracle_setup(dict(kind=kind, n=n, k=k))
+    _ORACLE.update(O=O, H=H, q=q, N=N, setup=time.time() - t0)
+
+
+def _oracle_time(args):
+    """The oracle's GMRES(60) on the full-size operator: cycles of `cycle_iters`
+    iterations until `seconds` are spent (at least one cycle)."""
+    seconds, cycle_iters = args
+    O, H, q = _ORACLE["O"], _ORACLE["H"], _ORACLE["q"]
+    it_total, t_run, x = 0, 0.0, None
+    while t_run < seconds or it_total == 0:
+        t1 = time.time()
+        x, it, _ = O.gmres(H, q, tol=1e-30, restart=60, maxiter=cycle_iters, x0=x)
+        t_run += time.time() - t1
+        it_total += it
+    return dict(iters=it_total, seconds=t_run, setup=_ORACLE["setup"], grid=_ORACLE["N"])
+
+
+class OraclePool:
+    """Spawned single-thread processes holding the oracle's full-size operator
+    (as many as the host cores and memory allow)."""
+
+    def __init__(self, kind, n):
+        import multiprocessing as mp
+        per_proc_gb = 13.0 if kind == "multifreq192" else 1.5  # GMRES(60) basis + operator per process
+        mem = _host_mem_gb()
+        self.procs = max(1, min(os.cpu_count() or 1, 16, int(mem // per_proc_gb) if mem else 16))
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"  # one BLAS thread per spawned process (set before the children import numpy)
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_oracle_init, initargs=(kind, n))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def sample(self, seconds, cycle_iters):
+        return self.pool.map(_oracle_time, [(seconds, cycle_iters)] * self.procs, chunksize=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _iteration_counts(kind, n):
+    name = "gmres_iterations_3d_multifreq_32.json" if kind == "multifreq192" else f"gmres_iterations_3d_layered_{n}.json"
+    path = os.path.join(ROOT, "oracle", "data", name)
+    if not os.path.exists(path):
+        return None, path
+    with open(path) as fh:
+        d = json.load(fh)
+    if kind == "multifreq192":
+        return float(d["iterations_per_pair"]), path
+    return float(d["forward_iterations"] + d["adjoint_iterations"]), path
+
+
+def cpu_baseline(kind, n, seconds, cycle_iters=60, pool=None):
+    """(src.freq)/s of the oracle on the host cores: a bounded sample of GMRES(60)
+    iterations on the full-size operator, one spawned single-thread process per
+    core (as many as host memory allows), scaled by the oracle's own iteration
+    count for a forward + adjoint solve."""
+    per_pair_iters, path = _iteration_counts(kind, n)
+    if per_pair_iters is None:
+        return None
+    own = pool is None
+    if own:
+        pool = OraclePool(kind, n)
+    try:
+        res = pool.sample(seconds, cycle_iters)
     finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+        if own:
+            pool.close()
+    procs = pool.procs
     t_iter = float(np.mean([r["seconds"] / r["iters"] for r in res]))
-    pair_seconds = per_pair_iters * t_iter
-    value = procs / pair_seconds
+    value = procs / (per_pair_iters * t_iter)
+    grid = res[0]["grid"]
+    if kind == "multifreq192":
+        how = (f"the oracle's iteration count per pair ({per_pair_iters:.0f}, forward + adjoint to tol 1e-9, mean over "
+               f"the 8 frequencies) measured on the 32^3 crop of the same recipe ({os.path.basename(path)}); the count "
+               f"only grows with the grid, so this is an upper bound on the oracle's throughput")
+    else:
+        how = f"the oracle's {per_pair_iters:.0f} iterations for one forward + adjoint solve ({os.path.basename(path)})"
+    cyc = ("full GMRES(60) cycles" if cycle_iters >= 60 else
+           f"the first {cycle_iters} iterations of GMRES(60) cycles (the cheapest of a cycle, so the time per "
+           f"iteration is a lower bound)")
     return dict(value=value, unit=UNIT, cores=procs, kind="oracle",
-                sample=(f"{procs} spawned single-thread processes, each running the oracle's GMRES(60) on the "
-                        f"full {iters['grid']} operator for ~{seconds:.0f} s ({int(np.mean([r['iters'] for r in res]))} "
-                        f"iterations, {t_iter*1e3:.1f} ms each); scaled by the oracle's {per_pair_iters} iterations "
-                        f"for one forward + adjoint solve to tol {iters['tol']:g} "
-                        f"(oracle/data/{os.path.basename(path)}); assembly excluded"))
+                sample=(f"{procs} spawned single-thread processes, each timing {cyc} on the full {grid} operator "
+                        f"(~{max(seconds, 0):.0f} s, {int(np.mean([r['iters'] for r in res]))} iterations, "
+                        f"{t_iter*1e3:.0f} ms each; assembly {np.mean([r['setup'] for r in res]):.0f} s excluded), "
+                        f"scaled by {how}"))
 
 
 def run_reference(args):
@@ -243,16 +382,30 @@ def run_reference(args):
     if rank != 0:
         return
     steps = []
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.n, max(2.0, args.cpu_seconds / 3))
-        if i >= args.warmup:
-            steps.append(cb["value"])
+    big = args.workload == "multifreq192"
+    if _iteration_counts(args.workload, args.n)[0] is None:
+        print(json.dumps(dict(impl="reference", unavailable="the oracle's iteration counts are missing")))
+        return
+    pool = OraclePool(args.workload, args.n)
+    try:
+        for i in range(args.warmup + args.steps):
+            # multifreq192: each step times the first 3 iterations of a GMRES(60) cycle per process (cheaper
+            # than the cycle's mean, so the value is an upper bound)
+            cb = cpu_baseline(args.workload, args.n, 0.0 if big else max(2.0, args.cpu_seconds / 3),
+                              cycle_iters=3 if big else 60, pool=pool)
+            if i >= args.warmup:
+                steps.append(cb["value"])
+    finally:
+        pool.close()
     v = float(np.median(steps))
     cb["value"] = v
+    wl_name = ("3d-multifreq-192^3-h25-128src-8f (1 source x 8 frequencies)" if big
+               else f"3d-layered-{args.n}^3-h25-pml10-4Hz-16src")
+    units = 8 if big else 16
     line = dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * 16 / v, higher_is_better=True, scaling="weak",
+                warmup=args.warmup, ms_per_step=1e3 * units / v, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=f"3d-layered-{args.n}^3-h25-pml10-4Hz-16src", sources=16, freqs=1),
+                config=dict(workload=wl_name, pairs_per_step=units),
                 cpu_baseline=cb, e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -436,10 +589,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    big = args.workload == "multifreq192"
     # the oracle's process pool is spawned before the first GPU call
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.op == "misfit_grad":
-        cpu = cpu_baseline(args.n, args.cpu_seconds)
+        cpu = cpu_baseline(args.workload, args.n, args.cpu_seconds, cycle_iters=10 if big else 60)
 
     import torch
     import torch.distributed as dist
@@ -449,7 +603,7 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    wl = workload(args.n, rank, world)
+    wl, wl_name = make_workload(args, rank, world)
     levels = args.levels if args.precond == "mlgmres" else max(1, args.levels)
     grid = helm.make_grid(3, wl.n, wl.h, wl.npml, wl.v_ref, levels=levels)
     prec = {"mlgmres": helm.PRECOND_MLGMRES, "jacobi": helm.PRECOND_JACOBI, "none": helm.PRECOND_NONE}[args.precond]
@@ -459,16 +613,21 @@ def main():
                              k_inner=kin, tol=args.tol, max_cycles=400, tol_inner=args.tol_inner, max_refine=60,
                              reorth=args.reorth, k_so=kso, k_si=ksi, k_co=kco, k_ci=kci, max_batch=args.max_batch)
     plan = helm.Plan(grid, opts, device=dev)
-    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
     m0 = T(wl.m0.ravel(), torch.float64)
     src = T(wl.src_idx, torch.int32)
     Q = T(wl.Q, torch.complex128)
     rec = T(wl.rec_idx, torch.int32)
-    # observed data: FP64 forward modelling in the true model (input generation, untimed)
-    p64 = helm.Plan(grid, helm.default_opts(precision=helm.FP64, precond=helm.PRECOND_MLGMRES, tol=1e-13,
-                                            max_cycles=400), device=dev)
-    _, d_obs, _ = helm.helm_forward(p64, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
+    # observed data: forward modelling in the true model (input generation, untimed): FP64 on the 64^3 model,
+    # complex64 inner solves refined in FP64 to 1e-11 on the 192^3 one
+    ref_opts = dict(precond=helm.PRECOND_MLGMRES, max_cycles=400, k_so=kso, k_si=ksi, k_co=kco, k_ci=kci)
+    p_obs = helm.Plan(grid, helm.default_opts(precision=helm.MIXED if big else helm.FP64, tol=1e-11 if big else 1e-13,
+                                              **ref_opts), device=dev)
+    _, d_obs, _ = helm.helm_forward(p_obs, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
                                     want_fields=False)
+    p_obs.close()
+    del p_obs
+    torch.cuda.empty_cache()
     nsrc, nfreq = wl.nsrc, wl.nfreq
     units = nsrc * nfreq
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -478,19 +637,20 @@ def main():
     # a seeded model perturbation for the Hessian products (input, resident)
     dmv = T(np.random.default_rng(7).standard_normal(wl.m0.size) * 1e-9, torch.float64) if gn or hess else None
 
-    def step(p=plan, reduce=True, m=None, s_=None, q_=None, r_=None, d_=None, dm_=None):
+    def step(p=plan, reduce=True, m=None, s_=None, q_=None, r_=None, d_=None, dm_=None, freqs=None):
         m, s_, q_, r_ = (m0 if m is None else m), (src if s_ is None else s_), (Q if q_ is None else q_), \
             (rec if r_ is None else r_)
+        fr = wl.freqs_hz if freqs is None else freqs
         if gn or hess:
             dmx = dmv if dm_ is None else dm_
             if gn:
-                h, rep = helm.helm_gn_hessvec(p, m, wl.freqs_hz, s_, q_, r_, dmx)
+                h, rep = helm.helm_gn_hessvec(p, m, fr, s_, q_, r_, dmx)
             else:
-                h, rep = helm.helm_hessvec(p, m, wl.freqs_hz, s_, q_, r_, d_obs if d_ is None else d_, dmx)
+                h, rep = helm.helm_hessvec(p, m, fr, s_, q_, r_, d_obs if d_ is None else d_, dmx)
             if world > 1 and reduce:
                 dist.all_reduce(h)
             return None, h, rep
-        f, g, rep = helm.misfit_and_gradient(p, m, wl.freqs_hz, s_, q_, r_, d_obs if d_ is None else d_)
+        f, g, rep = helm.misfit_and_gradient(p, m, fr, s_, q_, r_, d_obs if d_ is None else d_)
         if world > 1 and reduce:
             dist.all_reduce(f)
             dist.all_reduce(g)
@@ -556,57 +716,93 @@ def main():
                    frac=round(st["bytes"] / (st["ms"] / 1e3) / 1e9 / hbm, 3),
                    launches=st["launches"], avg_launch_us=round(1e3 * st["ms"] / max(st["launches"], 1), 2))
 
-    out = dict(metric=METRIC_GN if gn else METRIC_HESS if hess else METRIC, value=round(value, 3), unit=UNIT,
+    cfg = dict(workload=wl_name if world == 1 else f"{wl_name}-x{world}ranks", grid_comp=list(plan.N),
+               pairs_per_step_per_rank=units, sources_per_rank=nsrc, freqs_hz=[round(float(x), 4) for x in wl.freqs_hz],
+               receivers=wl.nrec, precond=args.precond, levels=levels, k_inner=kin, smoother=args.smoother,
+               tol=args.tol, tol_inner=args.tol_inner, reorth=args.reorth, l2="flushed between timed steps (256 MB)",
+               parallelism=f"dp{world} over sources, f and g all-reduced" if world > 1 else "1 GPU",
+               op="J^T J dm (3 solves per pair)" if gn else
+               "full Hessian times dm (4 solves per pair)" if hess else "misfit + gradient (2 solves per pair)")
+    if big:
+        cfg["source_columns"] = wl.meta["columns"]
+    out = dict(metric=METRIC_GN if gn else METRIC_HESS if hess else METRIC, value=round(value, 4), unit=UNIT,
                n_gpus=world, steps=args.steps,
                warmup=args.warmup, ms_per_step=round(ms_max, 3), higher_is_better=True, scaling="weak",
                vs_baseline=None, dtype="c64 inner / f64 refine" if args.precision == "mixed" else "f64",
-               data="synthetic (seeded layered model, observed data modelled in FP64)",
-               config=dict(workload=wl.name if world == 1 else f"{wl.name}-x{world}ranks", grid_comp=list(plan.N),
-                           sources_per_rank=nsrc, freqs=nfreq, receivers=wl.nrec, precond=args.precond,
-                           levels=levels, k_inner=kin, smoother=args.smoother, tol=args.tol,
-                           tol_inner=args.tol_inner, reorth=args.reorth, l2="flushed between timed steps (256 MB)",
-                           parallelism=f"dp{world} over sources, f and g all-reduced" if world > 1 else "1 GPU",
-                           op="J^T J dm (3 solves per pair)" if gn else
-                           "full Hessian times dm (4 solves per pair)" if hess else "misfit + gradient (2 solves per pair)"),
-               roofline=roofline, stencil=stencil, gpu_launches=int(launches),
+               data=("synthetic (seeded layered model with inclusions; observed data modelled in the true model, "
+                     "complex64 inner / FP64 refinement to 1e-11)" if big else
+                     "synthetic (seeded layered model, observed data modelled in FP64)"),
+               config=cfg, roofline=roofline, stencil=stencil, gpu_launches=int(launches),
                solver=dict(outer_iters_per_pair=float(np.mean(iters)), refinements_per_pair=float(np.mean(refs)),
-                           max_rel_resid=float(max(r["rel_resid"] for r in rep))),
+                           max_rel_resid=float(max(r["rel_resid"] for r in rep)),
+                           iters_per_pair=iters),
+               step_ms=dict(median=round(float(np.median(times)), 3), min=round(float(np.min(times)), 3),
+                            max=round(float(np.max(times)), 3)),
                clocks=clk)
     if rank == 0:
         # accuracy against the FP64 GPU path (itself checked against the oracle in tests)
-        if args.precision == "mixed" and (gn or hess):
-            _, h64, _ = step(p=p64, reduce=False)
-            _, h1, _ = step(reduce=False)
-            out["accuracy"] = dict(reference="FP64 GPU path, FGMRES+ML-GMRES to rel. residual 1e-13",
-                                   hessvec_rel_err=float((h1 - h64).norm().item() / h64.norm().item()))
-        elif args.precision == "mixed":
-            f64, g64, _ = helm.misfit_and_gradient(p64, m0, wl.freqs_hz, src, Q, rec, d_obs)
-            f1, g1, _ = step(reduce=False)
-            out["accuracy"] = dict(
-                reference="FP64 GPU path, FGMRES+ML-GMRES to rel. residual 1e-13",
-                f_rel_err=float(abs(f1.item() - f64.item()) / abs(f64.item())),
-                g_rel_err=float((g1 - g64).norm().item() / g64.norm().item()))
+        if args.precision == "mixed" and not args.no_accuracy:
+            tol64 = 1e-11 if big else 1e-13
+            p64 = helm.Plan(grid, helm.default_opts(precision=helm.FP64, tol=tol64, **ref_opts), device=dev)
+            t0 = time.perf_counter()
+            if gn or hess:
+                _, h64, _ = step(p=p64, reduce=False)
+                _, h1, _ = step(reduce=False)
+                out["accuracy"] = dict(reference=f"FP64 GPU path, FGMRES+ML-GMRES to rel. residual {tol64:g}",
+                                       hessvec_rel_err=float((h1 - h64).norm().item() / h64.norm().item()))
+            else:
+                f64, g64, _ = step(p=p64, reduce=False)
+                f1, g1, _ = step(reduce=False)
+                out["accuracy"] = dict(
+                    reference=f"FP64 GPU path, FGMRES+ML-GMRES to rel. residual {tol64:g}, same pairs",
+                    f_rel_err=float(abs(f1.item() - f64.item()) / abs(f64.item())),
+                    g_rel_err=float((g1 - g64).norm().item() / g64.norm().item()))
+            torch.cuda.synchronize()
+            out["accuracy"]["reference_seconds"] = round(time.perf_counter() - t0, 1)
+            p64.close()
+            del p64
+            torch.cuda.empty_cache()
         if not args.no_fp64_baseline and not (gn or hess):
+            # plain FP64 solves, one right-hand side at a time, same preconditioner and tolerance; on the
+            # 192^3 model over the middle frequency's pair of the step (its mixed cost is near the step's mean)
             pb = helm.Plan(grid, helm.default_opts(precision=helm.FP64, precond=prec, k_inner=kin, tol=args.tol,
-                                                   max_cycles=400, max_batch=1), device=dev)
-            helm.misfit_and_gradient(pb, m0, wl.freqs_hz, src, Q, rec, d_obs)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            helm.misfit_and_gradient(pb, m0, wl.freqs_hz, src, Q, rec, d_obs)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t64 = e0.elapsed_time(e1)
-            out["fp64_per_source"] = dict(value=round(units / (t64 / 1e3), 3), unit=UNIT, ms_per_step=round(t64, 1),
-                                          speedup_of_value=round(value / (units / (t64 / 1e3)), 2),
-                                          what="FP64 FGMRES+same preconditioner, one right-hand side at a time")
+                                                   max_cycles=400, max_batch=1, k_so=kso, k_si=ksi, k_co=kco,
+                                                   k_ci=kci), device=dev)
+            if big:
+                kf = nfreq // 2
+                bfr, bd, bs, bq = wl.freqs_hz[kf:kf + 1], d_obs[kf:kf + 1, :1].contiguous(), src[:1], Q[:1, :1]
+                bunits = 1
+            else:
+                bfr, bd, bs, bq, bunits = wl.freqs_hz, d_obs, src, Q, units
+            helm.misfit_and_gradient(pb, m0, bfr, bs, bq, rec, bd)
+            t64 = []
+            for _ in range(max(1, args.fp64_calls)):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                helm.misfit_and_gradient(pb, m0, bfr, bs, bq, rec, bd)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t64.append(e0.elapsed_time(e1))
+            tm = float(np.median(t64))
+            rate = bunits / (tm / 1e3)
+            out["fp64_per_source"] = dict(
+                value=round(rate, 4), unit=UNIT, ms_per_call=round(tm, 1), calls=len(t64),
+                ms_all=[round(t, 1) for t in t64], pairs_per_call=bunits,
+                speedup_of_value=round(value / rate, 2),
+                what=("FP64 FGMRES + the same preconditioner and tolerance, one right-hand side at a time; median "
+                      "of the timed calls" + (f"; each call = the step's {wl.freqs_hz[kf]:.3f} Hz pair" if big else
+                                               "; each call = all pairs of the step")))
+            pb.close()
+            del pb
+            torch.cuda.empty_cache()
         # end to end through the public API with host buffers
         hm = torch.as_tensor(wl.m0.ravel(), dtype=torch.float64).pin_memory()
         hd = d_obs.cpu().pin_memory()
         hdm = dmv.cpu().pin_memory() if dmv is not None else None
         hs, hq, hr = src.cpu().pin_memory(), Q.cpu().pin_memory(), rec.cpu().pin_memory()
         e2e_t = []
-        for i in range(args.steps + 1):
+        for i in range(max(1, args.e2e_steps) + 1):
             flush.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -623,8 +819,8 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in (hm, hd, hs, hq, hr)) + \
             (hdm.numel() * hdm.element_size() if hdm is not None else 0)
         d2h = fh.numel() * 8 + gh.numel() * 8
-        out["e2e"] = dict(value=round(units / (np.mean(e2e_t) / 1e3), 3), unit=UNIT, h2d_bytes_per_step=int(h2d),
-                          d2h_bytes_per_step=int(d2h))
+        out["e2e"] = dict(value=round(units / (np.mean(e2e_t) / 1e3), 4), unit=UNIT, h2d_bytes_per_step=int(h2d),
+                          d2h_bytes_per_step=int(d2h), steps=len(e2e_t))
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)

@@ -66,6 +66,8 @@ typedef enum {
 } helm_status;
 
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
+/* Element type of stored forward fields (helm_misfit / helm_gradient). */
+typedef enum { HELM_FIELD_C128 = 0, HELM_FIELD_C64 = 1 } helm_field_type;
 typedef enum { HELM_PRECOND_NONE = 0, HELM_PRECOND_JACOBI = 1, HELM_PRECOND_MLGMRES = 2 } helm_precond;
 typedef enum {
   HELM_CALL_APPLY = 0, HELM_CALL_FORWARD = 1, HELM_CALL_ADJOINT = 2, HELM_CALL_MISFIT_GRAD = 3,
@@ -313,24 +315,29 @@ int helm_wri_misfit_and_gradient(helm_plan* plan, const double* m_phys, const do
  * policy of a differentiable objective):
  *   R_out  complex128 [nfreq][nsrc][nrec] or NULL: data residuals P_r u - d
  *          (rows of masked-out pairs are set to zero)
- *   U_out  complex128 [nfreq][nsrc][n_comp] or NULL: forward fields
- *          (masked-out pairs are not written)
- * Other arguments as misfit_and_gradient.  f_out float64 [1]. */
+ *   U_out  [nfreq][nsrc][n_comp] or NULL: forward fields (masked-out pairs
+ *          are not written), complex128 when u_type is HELM_FIELD_C128 or
+ *          complex64 when it is HELM_FIELD_C64 (each part of the FP64 field
+ *          rounded to nearest: half the memory, a relative perturbation of
+ *          at most 2^-24 per part, which the gradient inherits)
+ * The misfit itself always uses the FP64 field.  Other arguments as
+ * misfit_and_gradient.  f_out float64 [1]. */
 int helm_misfit(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
                 const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
                 const int32_t* rec_idx, int nrec, const void* d_obs, const uint8_t* mask, double* f_out,
-                void* R_out, void* U_out, void* workspace, size_t ws_bytes, helm_rhs_report* reports,
-                helm_stream_t stream);
+                void* R_out, void* U_out, int u_type, void* workspace, size_t ws_bytes,
+                helm_rhs_report* reports, helm_stream_t stream);
 
 /* Adjoint-state gradient from stored forward fields (Appendix A; Table
  * derivstuff, grad f = T* V): for every unmasked (k, s),
  *   v = -H(m, w_k)^{-H} P_r^T R_{k,s},   g = E^T sum w_k^2 Re(conj(U_{k,s}) v),
- * with U and R as written by helm_misfit (U complex128 [nfreq][nsrc][n_comp],
- * R complex128 [nfreq][nsrc][nrec]).  g_out float64 [n_phys] (overwritten).
- * helm_misfit followed by helm_gradient equals misfit_and_gradient. */
+ * with U and R as written by helm_misfit (U [nfreq][nsrc][n_comp] of type
+ * u_type, R complex128 [nfreq][nsrc][nrec]).  g_out float64 [n_phys]
+ * (overwritten).  helm_misfit followed by helm_gradient with complex128
+ * fields equals misfit_and_gradient. */
 int helm_gradient(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
                   const int32_t* rec_idx, int nrec, const void* R_in, int nsrc, const void* U_in,
-                  const uint8_t* mask, double* g_out, void* workspace, size_t ws_bytes,
+                  int u_type, const uint8_t* mask, double* g_out, void* workspace, size_t ws_bytes,
                   helm_rhs_report* reports, helm_stream_t stream);
 
 /* One model's misfit_and_gradient request for helm_misfit_and_gradient_batch
@@ -388,6 +395,26 @@ int helm_misfit_and_gradient_batch(helm_batch_item* items, int nitems, int nwork
 #define HELM_NOALLOC_SCRATCH_BYTES (16u << 20)
 int helm_apply_noalloc(helm_plan* plan, const double* m_phys, double freq_hz, int adjoint,
                        int precision, const void* x, void* y, int nrhs, helm_stream_t stream);
+
+/* Tile shapes of the operator apply (no counterpart in the paper: the
+ * paper's stencil is a CPU loop).  The complex64 apply has
+ * helm_stencil_variant_count() shapes -- columns per block, z-planes per tile
+ * and the blocks per SM its register budget is sized for, as
+ * helm_stencil_variant_info() reports.  Every shape computes every node with
+ * the same arithmetic, so results do not depend on the shape.  By default
+ * the first apply on a grid of at least 200000 nodes times each shape three
+ * times on that call's own fields (synchronising the stream once) and keeps
+ * the fastest for the grid; the complex128 apply and smaller grids use shape
+ * 0.  helm_stencil_select(v) forces shape v for every later apply (-1 goes
+ * back to tuning); HELM_E_INVAL for a shape out of range.
+ * helm_stencil_tuned() reports the shape tuned for a plan's grid level
+ * (plain apply when residual is 0, residual form b - H x otherwise) and the
+ * fastest launch time in microseconds, or HELM_E_INVAL when that grid has not
+ * been tuned.  The settings are process-wide. */
+int helm_stencil_variant_count(void);
+int helm_stencil_variant_info(int variant, int* threads, int* zplanes, int* min_blocks);
+int helm_stencil_select(int variant);
+int helm_stencil_tuned(const helm_plan* plan, int level, int residual, int* variant, double* us);
 
 /* Diagnostic (no counterpart in the paper): checks, on the device of the
  * current context, how the library reports a bounded device wait that runs

@@ -699,8 +699,13 @@ int helm_wri_misfit_and_gradient(helm_plan* P, const double* m_phys, const doubl
     for (int a = 0; a < nb; ++a) g[a] = start + a;
     if ((st = set_batch(c, g)) != HELM_OK) return st;
     std::vector<SlotReport> rep, r2;
+    // slots whose conjugate gradients still run (all in the first iteration, so
+    // every slot's correction field is defined; converged slots then stop
+    // taking solves and their reports stop changing)
+    std::vector<int> live(nb);
+    for (int a = 0; a < nb; ++a) live[a] = a;
     auto solve = [&](int dir, const double2* rhs, double2* out) {
-      st = solve_batch(c, dir, rhs, out, nb, r2);
+      st = solve_batch(c, dir, rhs, out, nb, r2, &live);
       if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return false;
       result = worst(result, st);
       merge_reports(rep, r2);
@@ -736,11 +741,12 @@ int helm_wri_misfit_and_gradient(helm_plan* P, const double* m_phys, const doubl
       cudaMemcpyAsync(rh.data(), c.rho, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.st);
       cudaMemcpyAsync(r0h.data(), c.rho0, sizeof(double) * nb, cudaMemcpyDeviceToHost, c.st);
       if (const int sc = sync_check(c); sc != HELM_OK) return sc;
-      converged = true;
+      live.clear();
       for (int a = 0; a < nb; ++a) {
         if (!std::isfinite(rh[a])) return HELM_E_NONFINITE;
-        if (rh[a] > thr2 * r0h[a]) converged = false;
+        if (rh[a] > thr2 * r0h[a]) live.push_back(a);
       }
+      converged = live.empty();
     }
     for (int a = 0; a < nb; ++a)
       if (rh[a] > thr2 * r0h[a] && r0h[a] > 0.0) rep[a].status = worst(rep[a].status, HELM_E_NOCONV);
@@ -784,11 +790,12 @@ int helm_gn_hessvec(helm_plan* P, const double* m_phys, const double* freqs_hz, 
 
 int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* src_idx,
                 int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
-                const void* d_obs, const uint8_t* mask, double* f_out, void* R_out, void* U_out, void* ws,
-                size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+                const void* d_obs, const uint8_t* mask, double* f_out, void* R_out, void* U_out, int u_type,
+                void* ws, size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out) return HELM_E_INVAL;
+  if (u_type != HELM_FIELD_C128 && u_type != HELM_FIELD_C64) return HELM_E_INVAL;
   Ctx c;
   if ((st = bind(P, HELM_CALL_MISFIT, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
   if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
@@ -818,7 +825,10 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
                            c.res, c.f_slot, c.st);
     launch_sum_f(c.f_slot, c.ident, nb, f_out, 1, c.st);
     if (R_out) launch_copy_fields(c.res, (double2*)R_out, c.ident, nb, c.slot_g, (size_t)nrec, c.st);
-    if (U_out) launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
+    if (U_out && u_type == HELM_FIELD_C64)
+      launch_copy_fields(c.u, (float2*)U_out, c.ident, nb, c.slot_g, n, c.st);
+    else if (U_out)
+      launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
     fill_reports(reports, g, rep);
   }
   if (const int sc = sync_check(c); sc != HELM_OK) return sc;
@@ -826,11 +836,12 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
 }
 
 int helm_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* rec_idx,
-                  int nrec, const void* R_in, int nsrc, const void* U_in, const uint8_t* mask, double* g_out,
-                  void* ws, size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+                  int nrec, const void* R_in, int nsrc, const void* U_in, int u_type, const uint8_t* mask,
+                  double* g_out, void* ws, size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!rec_idx || nrec < 1 || !R_in || !U_in || !g_out) return HELM_E_INVAL;
+  if (u_type != HELM_FIELD_C128 && u_type != HELM_FIELD_C64) return HELM_E_INVAL;
   Ctx c;
   if ((st = bind(P, HELM_CALL_GRADIENT, nfreq, nsrc, nrec, ws, ws_bytes, stream, c)) != HELM_OK) return st;
   if ((st = setup_operator(c, m_phys, freqs_hz)) != HELM_OK) return st;
@@ -855,7 +866,10 @@ int helm_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, in
     if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     for (auto& r : rep) result = worst(result, r.status);
-    launch_grad_accum((const double2*)U_in, c.slot_g, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    if (u_type == HELM_FIELD_C64)
+      launch_grad_accum((const float2*)U_in, c.slot_g, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
+    else
+      launch_grad_accum((const double2*)U_in, c.slot_g, c.v, c.w2_64, c.slot_f, c.ident, nb, n, c.gcomp, c.st);
     fill_reports(reports, g, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);

@@ -223,6 +223,9 @@ void launch_spread(const helm_plan& P, const double2* r, size_t r_stride, const 
                    int nrec, double sign, const int* slots, int nslots, double2* b, cudaStream_t st);
 void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
                        const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st, double scale = 1.0);
+// the same with complex64 forward fields
+void launch_grad_accum(const float2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
+                       const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st, double scale = 1.0);
 // WRI: receiver-space conjugate gradients (one slot per block) and helpers
 void launch_wri_init(const double2* res, int nrec, int nslots, double2* R, double2* Pd, double* rho, double* rho0,
                      cudaStream_t st);
@@ -248,6 +251,9 @@ void launch_extend_adjoint(const helm_plan& P, const double* gcomp, double* g_ph
 void launch_sum_f(const double* f_slot, const int* slots, int nslots, double* f_out, int accumulate,
                   cudaStream_t st);
 void launch_copy_fields(const double2* src, double2* dst, const int* slots, int nslots,
+                        const int* dst_index, size_t n, cudaStream_t st);
+// complex128 fields rounded to complex64
+void launch_copy_fields(const double2* src, float2* dst, const int* slots, int nslots,
                         const int* dst_index, size_t n, cudaStream_t st);
 void launch_check_finite(const double* vals, const int* act, int na, int* bad, cudaStream_t st);
 

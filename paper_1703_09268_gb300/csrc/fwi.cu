@@ -229,7 +229,10 @@ __global__ void k_spread(GeomArgs g, const double2* __restrict__ r, size_t r_str
 // gcomp[p] += sum_slots w_f^2 Re(conj(u) v), slots summed in order.  The
 // field u of slot s is u[u_idx[s]] when u_idx is given (fields stored by the
 // caller in (frequency, source) order), else u[s].
-__global__ void k_grad_accum(const double2* __restrict__ u, const int* __restrict__ u_idx,
+// U is complex128, or complex64 for forward fields stored at half the bytes
+// (promoted to FP64 before the product).
+template <typename CU>
+__global__ void k_grad_accum(const CU* __restrict__ u, const int* __restrict__ u_idx,
                              const double2* __restrict__ v, const double* __restrict__ w2,
                              const int* __restrict__ slot_f, const int* __restrict__ slots, int nslots,
                              size_t n, double scale, double* __restrict__ gcomp) {
@@ -238,9 +241,9 @@ __global__ void k_grad_accum(const double2* __restrict__ u, const int* __restric
   double acc = gcomp[p];
   for (int a = 0; a < nslots; ++a) {
     const int s = slots[a];
-    const double2 uu = u[(size_t)(u_idx ? u_idx[s] : s) * n + p];
+    const CU uu = u[(size_t)(u_idx ? u_idx[s] : s) * n + p];
     const double2 vv = v[(size_t)s * n + p];
-    acc += scale * w2[slot_f[s]] * (uu.x * vv.x + uu.y * vv.y);
+    acc += scale * w2[slot_f[s]] * ((double)uu.x * vv.x + (double)uu.y * vv.y);
   }
   gcomp[p] = acc;
 }
@@ -475,13 +478,19 @@ __global__ void k_sum_f(const double* __restrict__ f_slot, const int* __restrict
   *f_out = acc;
 }
 
-__global__ void k_copy_fields(const double2* __restrict__ src, double2* __restrict__ dst,
+// dst complex128 (a copy) or complex64 (each part rounded to nearest)
+template <typename CD>
+__global__ void k_copy_fields(const double2* __restrict__ src, CD* __restrict__ dst,
                               const int* __restrict__ slots, const int* __restrict__ dst_index,
                               size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int a = blockIdx.y;
-  dst[(size_t)dst_index[a] * n + i] = src[(size_t)slots[a] * n + i];
+  const double2 v = src[(size_t)slots[a] * n + i];
+  CD o;
+  o.x = v.x;
+  o.y = v.y;
+  dst[(size_t)dst_index[a] * n + i] = o;
 }
 
 }  // namespace
@@ -575,8 +584,17 @@ void launch_grad_accum(const double2* u, const int* u_idx, const double2* v, con
                        const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st, double scale) {
   if (nslots <= 0) return;
   ProfScope ps(PC_FWI, (double)nslots * n * 2 * sizeof(double2) + (double)n * 2 * sizeof(double), st);
-  k_grad_accum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n, scale,
-                                                            gcomp);
+  k_grad_accum<double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n,
+                                                                     scale, gcomp);
+  count_launch();
+}
+
+void launch_grad_accum(const float2* u, const int* u_idx, const double2* v, const double* w2, const int* slot_f,
+                       const int* slots, int nslots, size_t n, double* gcomp, cudaStream_t st, double scale) {
+  if (nslots <= 0) return;
+  ProfScope ps(PC_FWI, (double)nslots * n * (sizeof(float2) + sizeof(double2)) + (double)n * 2 * sizeof(double), st);
+  k_grad_accum<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, u_idx, v, w2, slot_f, slots, nslots, n,
+                                                                    scale, gcomp);
   count_launch();
 }
 
@@ -666,7 +684,15 @@ void launch_copy_fields(const double2* src, double2* dst, const int* slots, int 
                         const int* dst_index, size_t n, cudaStream_t st) {
   if (nslots <= 0) return;
   dim3 grd((unsigned)((n + 255) / 256), nslots);
-  k_copy_fields<<<grd, 256, 0, st>>>(src, dst, slots, dst_index, n);
+  k_copy_fields<double2><<<grd, 256, 0, st>>>(src, dst, slots, dst_index, n);
+  count_launch();
+}
+
+void launch_copy_fields(const double2* src, float2* dst, const int* slots, int nslots, const int* dst_index, size_t n,
+                        cudaStream_t st) {
+  if (nslots <= 0) return;
+  dim3 grd((unsigned)((n + 255) / 256), nslots);
+  k_copy_fields<float2><<<grd, 256, 0, st>>>(src, dst, slots, dst_index, n);
   count_launch();
 }
 

@@ -547,15 +547,23 @@ int precond_apply(Ctx& c, int dir, const void* x, void* z) {
   return sync_check(c);
 }
 
-int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep) {
+int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep,
+                const std::vector<int>* only) {
   const helm_plan& P = *c.P;
   const helm_solve_opts& o = P.o;
   c.dir = dir;
   const size_t n = P.lev[0].n;
   rep.assign(nb, SlotReport{});
-  std::vector<int> all(nb);
-  for (int i = 0; i < nb; ++i) all[i] = i;
+  std::vector<int> all;
+  if (only) {
+    all = *only;
+  } else {
+    all.resize(nb);
+    for (int i = 0; i < nb; ++i) all[i] = i;
+  }
+  const std::vector<int> solved = all;
   set_active(c, all);
+  if (c.na == 0) return HELM_OK;
   KrylovOut ko;
   ko.iters.assign(c.B, 0);
   int st = HELM_OK;
@@ -566,7 +574,7 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
     st = outer_solve<double>(c, q, u, o.tol, &ko, true);
     cudaMemcpyAsync(rn.data(), c.h64.inst[0].ks.rnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
     cudaMemcpyAsync(qn.data(), c.qn, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
-    for (int a = 0; a < nb; ++a) rep[a].refine = 1;
+    for (int a : solved) rep[a].refine = 1;
   } else {
     // FP64 iterative refinement around complex64 inner solves:
     //   r = q - H u (FP64), e = H^{-1}(r/||r||) (complex64), u += ||r|| e (FP64)
@@ -602,12 +610,9 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
     }
   }
   if (const int sc = sync_check(c); sc != HELM_OK) return sc;
-  for (int a = 0; a < nb; ++a) {
+  for (int a : solved) {
     rep[a].iters = ko.iters[a];
     rep[a].rel = qn[a] > 0.0 ? rn[a] / qn[a] : 0.0;
-    if (!c.mixed) {
-      // rn holds the final residual norm copied after the solve
-    }
     if (!std::isfinite(rep[a].rel)) rep[a].status = HELM_E_NONFINITE;
     else if (rep[a].rel > o.tol) rep[a].status = HELM_E_NOCONV;
   }

@@ -115,9 +115,11 @@ int set_batch(Ctx& c, const std::vector<int>& g);
 // The same with explicit (frequency, source) per slot; g are the report indices.
 int set_batch_fs(Ctx& c, const std::vector<int>& g, const std::vector<int>& f, const std::vector<int>& s);
 void set_active(Ctx& c, const std::vector<int>& a);
-// Solve H u = q (dir 0) or H^H u = q (dir 1) for all slots of the batch;
-// q and u are FP64 batch arrays.  Fills rep[0..nb-1].
-int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep);
+// Solve H u = q (dir 0) or H^H u = q (dir 1) for all slots of the batch, or
+// only for the slots listed in `only`; q and u are FP64 batch arrays.  Fills
+// rep[0..nb-1] (slots left out keep an empty report and their u untouched).
+int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep,
+                const std::vector<int>* only = nullptr);
 int sync_check(Ctx& c);
 // z = M^{-1} x for the active slots (the plan's preconditioner, the plan's
 // precision; dir 1 uses the adjoint operator H^H).

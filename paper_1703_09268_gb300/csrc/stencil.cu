@@ -10,14 +10,21 @@
 // transposed, conjugated tables, so one kernel serves both directions.
 //
 // Layout: fields are x-fastest [Nz][Ny][Nx] per right-hand-side slot, slots
-// n apart.  A tile is STPB consecutive (x, y) columns of a plane (flattened,
-// so no lanes idle at ragged row ends) by ZRUN planes; each thread marches its
-// column in z, keeps the z-1 / z / z+1 values in registers and issues the
-// loads of the next plane before computing the current one; x and y
-// neighbours come through L1.  Blocks loop over tiles so the number of blocks
-// per slot is bounded, which lets the kernel also reduce its output: dot
-// products with Krylov basis vectors (the first Gram-Schmidt pass of an
-// Arnoldi step) or the norm of a residual (reduce.cuh).
+// n apart.  A tile is a run of consecutive (x, y) columns of a plane
+// (flattened, so no lanes idle at ragged row ends) by a run of z-planes; each
+// thread marches its column in z, keeps the z-1 / z / z+1 values in registers
+// and issues the loads of the next plane before computing the current one; x
+// and y neighbours come through L1.  The plain apply has several tile shapes
+// and picks one per grid by timing them on first use (or takes the one
+// helm_stencil_select forces).  The reducing apply loops its blocks over tiles
+// so the number of blocks per slot is bounded, which lets the kernel also
+// reduce its output: dot products with Krylov basis vectors (the first
+// Gram-Schmidt pass of an Arnoldi step) or the norm of a residual
+// (reduce.cuh).
+#include <array>
+#include <map>
+#include <mutex>
+
 #include "reduce.cuh"
 #include "tma.cuh"
 
@@ -35,32 +42,39 @@ struct TileGeom {
   int Nmax;
 };
 
-// Plain apply (no reduction): one tile per block, grid (tiles, active slots).
-// The tile's z coefficients sit in shared memory and, in single precision,
-// the z march is fully unrolled (no register rotation between planes).  With
-// PF > 0 (x 16-byte aligned) thread 0 bulk-prefetches into L2, one plane at a
-// time, the tile's window of x PF planes ahead of the march: the bytes in
-// flight no longer depend on registers.
-template <typename R, bool RESID, int PF>
-__global__ void __launch_bounds__(STPB, 6)
+// Plain apply (no reduction): one tile of TPB consecutive (x, y) columns by
+// ZR planes per block, on a 1D grid whose block index runs over the active
+// slots fastest, so the blocks that share a tile of m (and of the damping
+// tables) run back to back and m is fetched from HBM about once per launch
+// rather than once per slot.  The tile's z coefficients sit in shared memory
+// and, in single precision, the z march is fully unrolled (no register
+// rotation between planes).  With PF > 0 (x 16-byte aligned) thread 0
+// bulk-prefetches into L2, one plane at a time, the tile's window of x PF
+// planes ahead of the march: the bytes in flight no longer depend on
+// registers.  TPB, ZR and MINB (blocks per SM the register budget is sized
+// for) are the variants the launch-time tuner chooses between.
+template <typename R, bool RESID, int PF, int TPB, int ZR, int MINB>
+__global__ void __launch_bounds__(TPB, MINB)
 k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
                 const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
                 const R* __restrict__ m, const R* __restrict__ w2, const int* __restrict__ slot_f,
-                const int* __restrict__ act, TileGeom G) {
+                const int* __restrict__ act, int na, TileGeom G) {
   using C = cplx<R>;
-  __shared__ C stz[3][ZRUN];
+  __shared__ C stz[3][ZR];
   const int planei = G.K0 * G.K1;
-  const int seg = blockIdx.x % G.nseg;
-  const int zc = blockIdx.x / G.nseg;
-  const int p2 = seg * STPB + threadIdx.x;
-  const int s = act[blockIdx.y];
+  const int a = (int)(blockIdx.x % (unsigned)na);
+  const int tile = (int)(blockIdx.x / (unsigned)na);
+  const int seg = tile % G.nseg;
+  const int zc = tile / G.nseg;
+  const int p2 = seg * TPB + threadIdx.x;
+  const int s = act[a];
   const int f = slot_f[s];
   const C* T = tab + (size_t)f * 9 * G.Nmax;
   const C* Tz = T + 6 * G.Nmax;
-  const int z0 = zc * ZRUN;
-  const int z1 = min(z0 + ZRUN, G.K2);
-  if (threadIdx.x < 3 * ZRUN) {
-    const int k = threadIdx.x / ZRUN, zz = threadIdx.x % ZRUN;
+  const int z0 = zc * ZR;
+  const int z1 = min(z0 + ZR, G.K2);
+  if (threadIdx.x < 3 * ZR) {
+    const int k = threadIdx.x / ZR, zz = threadIdx.x % ZR;
     stz[k][zz] = z0 + zz < G.K2 ? Tz[k * G.Nmax + z0 + zz] : mkc(R(0), R(0));
   }
   __syncthreads();
@@ -91,8 +105,8 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
   C next = (z0 + 1 < G.K2) ? xq[P] : zero;
   C w = hw ? xq[-1] : zero, ea = he ? xq[1] : zero, so = hs ? xq[-K0] : zero, no = hn ? xq[K0] : zero;
   R mm = mq[0];
-#pragma unroll(sizeof(R) == 4 ? ZRUN : 1)
-  for (int zz = 0; zz < ZRUN; ++zz) {
+#pragma unroll(sizeof(R) == 4 ? ZR : 1)
+  for (int zz = 0; zz < ZR; ++zz) {
     const int z = z0 + zz;
     if (z >= z1) break;
     const C* xn = xq + P;  // plane z+1
@@ -107,12 +121,12 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
       m2 = mq[P];
     }
     if (PF > 0 && threadIdx.x == 0 && z + PF < G.K2) {
-      // plane z+PF, columns [seg*STPB - K0, seg*STPB + STPB + K0) clipped to the plane, rounded out
+      // plane z+PF, columns [seg*TPB - K0, seg*TPB + TPB + K0) clipped to the plane, rounded out
       // to 16-byte bounds without leaving this slot's field (the element before an odd-aligned
       // field start belongs to the previous slot, or the start is even)
       const size_t fb = (size_t)s * G.n, pz = fb + (size_t)(z + PF) * P;
-      const size_t lo = pz + (size_t)max(0, seg * STPB - K0);
-      const size_t hi = pz + (size_t)min(P, seg * STPB + STPB + K0);
+      const size_t lo = pz + (size_t)max(0, seg * TPB - K0);
+      const size_t hi = pz + (size_t)min(P, seg * TPB + TPB + K0);
       const size_t a0 = lo & ~(size_t)1;
       size_t a1 = (hi + 1) & ~(size_t)1;
       if (a1 > fb + G.n) a1 -= 2;
@@ -335,6 +349,99 @@ void stencil_red(dim3 grd, cudaStream_t st, const OpView<R>& op, const int* slot
     stencil_go<R, RESID, KMAX + 1>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
 }
 
+// Shapes of the plain apply the tuner chooses between: threads per block
+// (consecutive columns of a plane), z-planes per tile, blocks per SM the
+// register budget is sized for.
+struct PlainShape {
+  int tpb, zr, minb;
+};
+constexpr PlainShape kPlain[] = {{128, 16, 6}, {128, 16, 8}, {128, 32, 6}, {256, 16, 3}, {128, 8, 8}, {256, 8, 4}};
+constexpr int kNumPlain = (int)(sizeof(kPlain) / sizeof(kPlain[0]));
+
+std::atomic<int> g_plain_forced{-1};  // >= 0: every plain apply uses this shape
+std::mutex g_tune_mu;
+struct TuneRec {
+  int variant;
+  float us;
+};
+std::map<std::array<int, 5>, TuneRec> g_plain_choice;  // (K0, K1, K2, residual, prefetch) -> choice
+
+template <typename R, bool RESID, int PF, int TPB, int ZR, int MINB>
+void plain_go(cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* x,
+              Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y) {
+  TileGeom G;
+  G.K0 = op.K[0];
+  G.K1 = op.K[1];
+  G.K2 = op.K[2];
+  G.nseg = (int)(((size_t)G.K0 * G.K1 + TPB - 1) / TPB);
+  G.nzc = (G.K2 + ZR - 1) / ZR;
+  G.ntiles = G.nseg * G.nzc;
+  G.n = op.n;
+  G.Nmax = op.Nmax;
+  const unsigned nblk = (unsigned)G.ntiles * (unsigned)na;
+  k_stencil_plain<R, RESID, PF, TPB, ZR, MINB><<<nblk, TPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab,
+                                                                      op.m, op.w2, slot_f, act, na, G);
+  count_launch();
+}
+
+template <typename R, bool RESID, int PF>
+void plain_variant(int v, cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act, int na,
+                   const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y) {
+  if (sizeof(R) == 8) v = 0;  // the FP64 apply is bound by the FP64 pipe: one shape
+  switch (v) {
+    case 1: plain_go<R, RESID, PF, 128, 16, 8>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    case 2: plain_go<R, RESID, PF, 128, 32, 6>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    case 3: plain_go<R, RESID, PF, 256, 16, 3>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    case 4: plain_go<R, RESID, PF, 128, 8, 8>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    case 5: plain_go<R, RESID, PF, 256, 8, 4>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    default: plain_go<R, RESID, PF, 128, 16, 6>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+  }
+}
+
+// The shape for this grid: the forced one, else the tuned one, tuning on first
+// use.  Tuning launches every shape on the call's own fields (each launch
+// writes the same y: every shape computes every point with the same
+// arithmetic, so the results are bitwise identical) and keeps the fastest of
+// three timed launches per shape; it synchronises the stream once per grid.
+template <typename R, bool RESID, int PF>
+int plain_choose(cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* x,
+                 Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y) {
+  const int forced = g_plain_forced.load();
+  if (forced >= 0) return forced;
+  if (sizeof(R) == 8 || op.n < PROF_COARSE_N) return 0;  // FP64, or grids that sit in L2: no tuning
+  const std::array<int, 5> key{op.K[0], op.K[1], op.K[2], RESID ? 1 : 0, PF};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_plain_choice.find(key);
+  if (it != g_plain_choice.end()) return it->second.variant;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return 0;
+  }
+  int best = 0;
+  float best_ms = 1e30f;
+  for (int v = 0; v < kNumPlain; ++v) {
+    plain_variant<R, RESID, PF>(v, st, op, slot_f, act, na, x, xs, b, bs, y);  // warm
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      plain_variant<R, RESID, PF>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
+      cudaEventRecord(e1, st);
+      float ms = 1e30f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        tmin = std::min(tmin, ms);
+    }
+    if (tmin < best_ms) {
+      best_ms = tmin;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_plain_choice[key] = TuneRec{best, 1e3f * best_ms};
+  return best;
+}
+
 }  // namespace
 
 template <typename R>
@@ -345,6 +452,22 @@ void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int 
   Epi e = epi ? *epi : Epi{};
   double by = (double)na * op.n * (b ? 3 : 2) * sizeof(cplx<R>) + (double)op.n * sizeof(R);
   if (e.kind == EPI_DOTS) by += (double)na * op.n * nv * sizeof(cplx<R>);
+  if (e.kind == EPI_NONE) {
+    // L2 prefetch 4 planes ahead: single precision (the FP64 stencil is ALU-bound), 16-byte aligned x,
+    // grids that do not sit in L2 anyway.  The shape is chosen (tuned on first use) outside the timed scope.
+    const bool pf = sizeof(R) == 4 && ((uintptr_t)x & 15) == 0 && op.n >= PROF_COARSE_N;
+    int v;
+    if (b && pf) v = plain_choose<R, true, 4>(st, op, slot_f, act, na, x, xs, b, bs, y);
+    else if (b) v = plain_choose<R, true, 0>(st, op, slot_f, act, na, x, xs, b, bs, y);
+    else if (pf) v = plain_choose<R, false, 4>(st, op, slot_f, act, na, x, xs, b, bs, y);
+    else v = plain_choose<R, false, 0>(st, op, slot_f, act, na, x, xs, b, bs, y);
+    ProfScope ps(prof_stencil_class<R>(op.n), by, st);
+    if (b && pf) plain_variant<R, true, 4>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
+    else if (b) plain_variant<R, true, 0>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
+    else if (pf) plain_variant<R, false, 4>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
+    else plain_variant<R, false, 0>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
+    return;
+  }
   ProfScope ps(prof_stencil_class<R>(op.n), by, st);
   TileGeom G;
   G.K0 = op.K[0];
@@ -355,32 +478,13 @@ void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int 
   G.ntiles = G.nseg * G.nzc;
   G.n = op.n;
   G.Nmax = op.Nmax;
-  int nblk = G.ntiles;
-  if (e.kind != EPI_NONE) {
-    // bounded blocks per slot: every block reduces into one partial row
-    const int target = (152 * 12 + na - 1) / na;
-    nblk = std::min(G.ntiles, std::max(1, target));
-    const int rows = std::max(RED_BLOCKS_MAX, na);
-    if ((long long)nblk * na > rows) nblk = std::max(1, rows / na);
-  }
+  // bounded blocks per slot: every block reduces into one partial row
+  const int target = (152 * 12 + na - 1) / na;
+  int nblk = std::min(G.ntiles, std::max(1, target));
+  const int rows = std::max(RED_BLOCKS_MAX, na);
+  if ((long long)nblk * na > rows) nblk = std::max(1, rows / na);
   dim3 grd(nblk, na);
-  if (e.kind == EPI_NONE) {
-    // L2 prefetch 4 planes ahead: single precision (the FP64 stencil is ALU-bound), 16-byte aligned x,
-    // grids that do not sit in L2 anyway
-    const bool pf = sizeof(R) == 4 && ((uintptr_t)x & 15) == 0 && op.n >= PROF_COARSE_N;
-    if (b && pf)
-      k_stencil_plain<R, true, 4><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
-                                                        op.w2, slot_f, act, G);
-    else if (b)
-      k_stencil_plain<R, true, 0><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
-                                                        op.w2, slot_f, act, G);
-    else if (pf)
-      k_stencil_plain<R, false, 4><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
-                                                         op.w2, slot_f, act, G);
-    else
-      k_stencil_plain<R, false, 0><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
-                                                         op.w2, slot_f, act, G);
-  } else if (b) {
+  if (b) {
     stencil_red<R, true>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
   } else {
     stencil_red<R, false>(grd, st, op, slot_f, act, x, xs, b, bs, y, G, V, vstride, nv, e);
@@ -423,3 +527,40 @@ INST(double)
 #undef INST
 
 }  // namespace helm
+
+using namespace helm;
+
+extern "C" {
+
+int helm_stencil_variant_count(void) { return kNumPlain; }
+
+int helm_stencil_variant_info(int variant, int* threads, int* zplanes, int* min_blocks) {
+  if (variant < 0 || variant >= kNumPlain) return HELM_E_INVAL;
+  if (threads) *threads = kPlain[variant].tpb;
+  if (zplanes) *zplanes = kPlain[variant].zr;
+  if (min_blocks) *min_blocks = kPlain[variant].minb;
+  return HELM_OK;
+}
+
+int helm_stencil_select(int variant) {
+  if (variant < -1 || variant >= kNumPlain) return HELM_E_INVAL;
+  g_plain_forced.store(variant);
+  return HELM_OK;
+}
+
+int helm_stencil_tuned(const helm_plan* plan, int level, int residual, int* variant, double* us) {
+  if (!plan || level < 0 || level >= MAX_LEVELS || !variant) return HELM_E_INVAL;
+  const LevelGeom& L = plan->lev[level];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int pf : {4, 0}) {
+    auto it = g_plain_choice.find(std::array<int, 5>{L.K[0], L.K[1], L.K[2], residual ? 1 : 0, pf});
+    if (it != g_plain_choice.end()) {
+      *variant = it->second.variant;
+      if (us) *us = it->second.us;
+      return HELM_OK;
+    }
+  }
+  return HELM_E_INVAL;
+}
+
+}  // extern "C"

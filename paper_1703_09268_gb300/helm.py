@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libhelm.so")
 HELM_OK, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_CUDA, HELM_E_NOCONV, HELM_E_NONFINITE, HELM_E_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
+FIELD_C128, FIELD_C64 = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2
 CALL_APPLY, CALL_FORWARD, CALL_ADJOINT, CALL_MISFIT_GRAD, CALL_MISFIT, CALL_GRADIENT, CALL_PRECOND = \
     0, 1, 2, 3, 4, 5, 6
@@ -63,7 +64,8 @@ EXPORTS = ["helm_default_opts", "helm_misfit_and_gradient_batch", "helm_plan_cre
            "helm_misfit", "helm_gradient", "helm_born", "helm_born_adjoint", "helm_gn_hessvec", "helm_hessvec",
            "helm_misfit_and_gradient_25d", "helm_wri_misfit_and_gradient",
            "helm_status_string", "helm_kernel_launch_count", "helm_profile_enable", "helm_profile_read",
-           "helm_check_bounded_wait"]
+           "helm_check_bounded_wait", "helm_stencil_variant_count", "helm_stencil_variant_info",
+           "helm_stencil_select", "helm_stencil_tuned"]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -95,12 +97,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  P, I, P, I, P, P, I, P, P, P, P, S, ctypes.POINTER(HelmRhsReport), P]
     lib.helm_wri_misfit_and_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, D, D, I, P, P, P,
                                                  S, ctypes.POINTER(HelmRhsReport), P]
-    lib.helm_misfit.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, P, S,
+    lib.helm_misfit.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, P, I, P, S,
                                 ctypes.POINTER(HelmRhsReport), P]
-    lib.helm_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, P, P, S,
+    lib.helm_gradient.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, I, P, P, P, S,
                                   ctypes.POINTER(HelmRhsReport), P]
     lib.helm_misfit_and_gradient_batch.argtypes = [ctypes.POINTER(HelmBatchItem), I, I]
     lib.helm_check_bounded_wait.argtypes = [P]
+    lib.helm_stencil_variant_count.argtypes = []
+    lib.helm_stencil_variant_info.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.helm_stencil_select.argtypes = [I]
+    lib.helm_stencil_tuned.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.helm_status_string.argtypes = [I]
     lib.helm_status_string.restype = ctypes.c_char_p
     lib.helm_kernel_launch_count.argtypes = []
@@ -286,6 +292,29 @@ def helm_precond_apply(plan: Plan, m_phys: torch.Tensor, freq_hz: float, x: torc
     _check(lib().helm_precond_apply(plan._h, _ptr(m_phys), float(freq_hz), int(bool(adjoint)), _ptr(x), _ptr(z),
                                     nrhs, ws, nb, _stream(x.device)), "helm_precond_apply")
     return z
+
+
+def stencil_variants() -> list:
+    """Tile shapes of the complex64 operator apply: dicts of threads, zplanes, min_blocks."""
+    out = []
+    for v in range(int(lib().helm_stencil_variant_count())):
+        t, z, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().helm_stencil_variant_info(v, ctypes.byref(t), ctypes.byref(z), ctypes.byref(b)),
+               "helm_stencil_variant_info")
+        out.append(dict(threads=t.value, zplanes=z.value, min_blocks=b.value))
+    return out
+
+
+def stencil_select(variant: int):
+    """Force tile shape `variant` for every later apply (-1: tune per grid on first use)."""
+    _check(lib().helm_stencil_select(int(variant)), "helm_stencil_select")
+
+
+def stencil_tuned(plan: "Plan", level: int = 0, residual: bool = False):
+    """(shape, microseconds) tuned for the plan's grid level, or None when not tuned yet."""
+    v, us = ctypes.c_int(), ctypes.c_double()
+    code = lib().helm_stencil_tuned(plan._h, int(level), int(bool(residual)), ctypes.byref(v), ctypes.byref(us))
+    return (v.value, us.value) if code == HELM_OK else None
 
 
 def check_bounded_wait(device="cuda") -> int:
@@ -520,10 +549,12 @@ def wri_misfit_and_gradient(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d
 
 
 def helm_misfit(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavelet=None, mask=None,
-                keep_residuals=False, keep_fields=False, f_out=None):
+                keep_residuals=False, keep_fields=False, f_out=None, field_dtype=torch.complex128):
     """f only (one solve per pair); optionally the data residuals R [nfreq, nsrc, nrec]
-    and forward fields U [nfreq, nsrc, n_comp] the gradient needs.
+    and forward fields U [nfreq, nsrc, n_comp] the gradient needs, stored as
+    `field_dtype` (complex128, or complex64 at half the memory).
     Returns (f, R or None, U or None, reports)."""
+    _need(field_dtype in (torch.complex128, torch.complex64), "field_dtype must be complex128 or complex64")
     _dev(m_phys, torch.float64, "m_phys")
     _dev(src_idx, torch.int32, "src_idx")
     _dev(Q, torch.complex128, "Q")
@@ -543,22 +574,27 @@ def helm_misfit(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, d_obs, wavele
     dev = m_phys.device
     f = torch.empty(1, dtype=torch.float64, device=dev) if f_out is None else f_out
     R = torch.empty((nfreq, nsrc, nrec), dtype=torch.complex128, device=dev) if keep_residuals else None
-    U = torch.zeros((nfreq, nsrc, plan.n_comp), dtype=torch.complex128, device=dev) if keep_fields else None
+    U = torch.zeros((nfreq, nsrc, plan.n_comp), dtype=field_dtype, device=dev) if keep_fields else None
+    u_type = FIELD_C64 if field_dtype == torch.complex64 else FIELD_C128
     rep = _reports(nfreq * nsrc)
     ws, nb = plan.workspace(plan.workspace_size(CALL_MISFIT, nfreq, nsrc, nrec))
     code = lib().helm_misfit(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx), src_idx.numel(),
                              _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(d_obs), _ptr(mask), _ptr(f),
-                             _ptr(R), _ptr(U), ws, nb, rep, _stream(dev))
+                             _ptr(R), _ptr(U), u_type, ws, nb, rep, _stream(dev))
     _check(code, "helm_misfit", allow_noconv=True)
     return f, R, U, reports_to_list(rep)
 
 
 def helm_gradient(plan: Plan, m_phys, freqs_hz, rec_idx, R, U, mask=None, g_out=None):
-    """Adjoint-state gradient from stored residuals R and fields U (helm_misfit)."""
+    """Adjoint-state gradient from stored residuals R and fields U (helm_misfit);
+    U may be complex128 or complex64."""
     _dev(m_phys, torch.float64, "m_phys")
     _dev(rec_idx, torch.int32, "rec_idx")
     _dev(R, torch.complex128, "R")
-    _dev(U, torch.complex128, "U")
+    _need(isinstance(U, torch.Tensor) and U.dtype in (torch.complex128, torch.complex64),
+          "U must be complex128 or complex64")
+    _dev(U, U.dtype, "U")
+    u_type = FIELD_C64 if U.dtype == torch.complex64 else FIELD_C128
     _check_common(plan, m_phys)
     nfreq, nsrc, nrec = R.shape
     _need(nfreq == len(np.atleast_1d(freqs_hz)) and nrec == rec_idx.numel(), "R must be [nfreq, nsrc, nrec]")
@@ -571,7 +607,7 @@ def helm_gradient(plan: Plan, m_phys, freqs_hz, rec_idx, R, U, mask=None, g_out=
     rep = _reports(nfreq * nsrc)
     ws, nb = plan.workspace(plan.workspace_size(CALL_GRADIENT, nfreq, nsrc, nrec))
     code = lib().helm_gradient(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(rec_idx), nrec, _ptr(R), nsrc,
-                               _ptr(U), _ptr(mask), _ptr(g), ws, nb, rep, _stream(dev))
+                               _ptr(U), u_type, _ptr(mask), _ptr(g), ws, nb, rep, _stream(dev))
     _check(code, "helm_gradient", allow_noconv=True)
     return g, reports_to_list(rep)
 

@@ -238,6 +238,21 @@ def workload_3d_multifreq(seed: int = 5, n: int = 192, h: float = 25.0, npml: in
         meta={"seed": seed})
 
 
+def centre_source(wl: Workload) -> int:
+    """Index of the source column whose node lies nearest the centre of the surface."""
+    nx, ny, _ = wl.n
+    loc = wl.src_idx[np.argmax(np.abs(wl.Q), axis=0)]
+    ix, iy = loc % nx, (loc // nx) % ny
+    return int(np.argmin((ix - (nx - 1) / 2.0) ** 2 + (iy - (ny - 1) / 2.0) ** 2))
+
+
+def source_subset(wl: Workload, cols) -> tuple:
+    """(src_idx, Q) of the listed source columns only (point sources)."""
+    cols = list(cols)
+    rows = np.nonzero(np.any(wl.Q[:, cols] != 0, axis=1))[0]
+    return wl.src_idx[rows].astype(np.int32), np.ascontiguousarray(wl.Q[np.ix_(rows, cols)])
+
+
 def batch_models(seed: int = 3, sizes=(48, 64, 80, 96, 112, 128, 144, 160), h: float = 25.0,
                  npml: int = 10) -> List[Workload]:
     """Eight models of uneven size, smooth random velocity in [1500, 4500] m/s,

@@ -6,7 +6,8 @@ on a 2x2 surface grid and 2 frequencies (2 and 4 Hz).  Observed data are the
 oracle's forward modelling in the true model; f and g are the oracle's
 adjoint-state misfit and gradient (sparse LU) at the smoothed model.  The
 fixture keeps f, ||g||, 512 seeded samples of g and 8 seeded random
-projections <g, r_k>, enough to compare a full gradient without storing it.
+projections <g, r_k> (crop32_gradient.json) and the whole gradient
+(crop32_gradient_full.npz, compared element by element).
 
     python tests/golden/make_crop32.py     (about 5 minutes on one core)
 """
@@ -53,6 +54,7 @@ def main():
         json.dump(out, fh)
     # the oracle's observed data, the input both sides use
     np.savez_compressed(os.path.join(HERE, "crop32_dobs.npz"), d_obs=d)
+    np.savez_compressed(os.path.join(HERE, "crop32_gradient_full.npz"), g=gr, f=float(f))
     print("f", f, "|g|", out["g_norm"])
 
 

@@ -169,3 +169,20 @@ def test_new_calls_reject_bad_arguments_before_any_device_work(helm):
     assert L.helm_wri_misfit_and_gradient(p3._h, fake, fr, 1, *wargs, 0.0, 1e-10, 10, *tail) == helm.HELM_E_INVAL
     assert L.helm_wri_misfit_and_gradient(p3._h, fake, fr, 1, *wargs, 1e3, 0.0, 10, *tail) == helm.HELM_E_INVAL
     assert L.helm_wri_misfit_and_gradient(p3._h, fake, fr, 1, *wargs, 1e3, 1e-10, 0, *tail) == helm.HELM_E_INVAL
+
+
+def test_stored_field_type_is_checked_before_any_device_work(helm):
+    """helm_misfit / helm_gradient accept complex128 or complex64 stored fields
+    and refuse any other field type code with HELM_E_INVAL on the host."""
+    L = helm.lib()
+    p3 = helm.Plan(helm.make_grid(3, (8, 8, 8), 25.0, (2, 2, 2), 3000.0), helm.default_opts(precond=0),
+                   device="cpu")
+    fr = (ctypes.c_double * 1)(5.0)
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks fail before any use
+    rep = (helm.HelmRhsReport * 1)()
+    assert helm.FIELD_C128 == 0 and helm.FIELD_C64 == 1
+    for bad in (-1, 2):
+        assert L.helm_misfit(p3._h, fake, fr, 1, fake, 1, fake, 1, None, fake, 1, fake, None, fake, None, fake, bad,
+                             fake, 1 << 20, rep, None) == helm.HELM_E_INVAL
+        assert L.helm_gradient(p3._h, fake, fr, 1, fake, 1, fake, 1, fake, bad, None, fake, fake, 1 << 20, rep,
+                               None) == helm.HELM_E_INVAL

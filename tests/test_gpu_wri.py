@@ -1,8 +1,11 @@
 """GPU parity of the WRI (penalty) objective and gradient (Sec. 3, Appendix B)
 with the oracle, whose field comes from a sparse LU of the normal equations.
 The GPU field comes from receiver-space conjugate gradients over H / H^H
-solves; the tolerance covers the CG stopping test (1e-12 relative residual,
-FP64) and, for mixed precision, the inner solves refined to 1e-11."""
+solves.  The CG stopping test (1e-14 relative residual with FP64 solves to
+3e-14; 1e-12 with mixed-precision solves refined to 1e-12) sits well below the
+parity bars of 1e-10 (FP64) and 1e-8 (mixed).  A run with two pairs per
+batch checks that the CG state is reset per batch and that f and g add up
+across batches."""
 import numpy as np
 import pytest
 import torch
@@ -45,17 +48,20 @@ def pw():
                 f_fwi=f_fwi)
 
 
-@pytest.mark.parametrize("name,opts,cg_tol,tol", [("fp64", dict(precision=0, precond=2, tol=1e-13), 1e-12, 1e-8),
-                                                  ("mixed", dict(precision=1, precond=2, tol=1e-11), 1e-10, 1e-6)])
+@pytest.mark.parametrize("name,opts,cg_tol,tol", [
+    ("fp64", dict(precision=0, precond=2, tol=3e-14), 1e-14, 1e-10),
+    ("mixed", dict(precision=1, precond=2, tol=1e-12), 1e-12, 1e-8),
+    ("fp64-two-per-batch", dict(precision=0, precond=2, tol=3e-14, max_batch=2), 1e-14, 1e-10)])
 def test_wri_misfit_gradient(helm, pw, name, opts, cg_tol, tol):
     p = pw
     plan = helm.Plan(helm.make_grid(2, p["n"], p["h"], p["npml"], 2500.0, levels=2), helm.default_opts(**opts),
                      device=DEV)
     f, g, rep = helm.wri_misfit_and_gradient(plan, T(p["m"], torch.float64), p["freqs"], T(p["src"], torch.int32),
                                              T(p["Q"], torch.complex128), T(p["rec"], torch.int32),
-                                             T(p["d"], torch.complex128), p["lam"], cg_tol=cg_tol, cg_maxit=200)
+                                             T(p["d"], torch.complex128), p["lam"], cg_tol=cg_tol, cg_maxit=400)
     fe = abs(f.item() - p["f"]) / abs(p["f"])
     ge = np.linalg.norm(g.cpu().numpy() - p["g"]) / np.linalg.norm(p["g"])
+    print(name, "f rel err", fe, "g rel err", ge, "solver iterations per pair", [r["iters"] for r in rep])
     assert fe <= tol and ge <= tol, (fe, ge, [r["iters"] for r in rep])
     # the penalty objective differs from the FWI misfit at this lambda (not the trivial limit)
     assert abs(p["f"] - p["f_fwi"]) > 0.05 * p["f_fwi"]
