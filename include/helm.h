@@ -180,12 +180,18 @@ int helm_precond_apply(helm_plan* plan, const double* m_phys, double freq_hz, in
  *   src_idx  int32 [n_srcloc]; Q complex128 [n_srcloc][nsrc]
  *   wavelet  complex128 [nfreq] or NULL (all ones)
  *   rec_idx  int32 [nrec]
+ *   U0       complex128 [nfreq][nsrc][n_comp] or NULL: initial guesses (a warm
+ *            start, e.g. the fields of a nearby model, as when an inversion
+ *            moves on between model updates or frequency bands); the solves
+ *            start from zero when NULL.  A guess whose residual already meets
+ *            the tolerance is returned unchanged after no iteration.  U0 may
+ *            be the same array as U_out.
  *   U_out    complex128 [nfreq][nsrc][n_comp] or NULL
  *   D_out    complex128 [nfreq][nsrc][nrec] or NULL
  *   reports  HOST [nfreq*nsrc] or NULL */
 int helm_forward(helm_plan* plan, const double* m_phys, const double* freqs_hz, int nfreq,
                  const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc,
-                 const void* wavelet, const int32_t* rec_idx, int nrec,
+                 const void* wavelet, const int32_t* rec_idx, int nrec, const void* U0,
                  void* U_out, void* D_out, void* workspace, size_t ws_bytes,
                  helm_rhs_report* reports, helm_stream_t stream);
 

@@ -310,8 +310,8 @@ static int check_indices(Ctx& c, const int32_t* src, int nsrcloc, const int32_t*
 
 int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
                  const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
-                 const int32_t* rec_idx, int nrec, void* U_out, void* D_out, void* ws, size_t ws_bytes,
-                 helm_rhs_report* reports, helm_stream_t stream) {
+                 const int32_t* rec_idx, int nrec, const void* U0, void* U_out, void* D_out, void* ws,
+                 size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || nrec < 0 || (nrec > 0 && !rec_idx)) return HELM_E_INVAL;
@@ -331,8 +331,10 @@ int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int
     cudaMemsetAsync(c.q, 0, sizeof(double2) * nb * n, c.st);
     launch_sources(*P, src_idx, n_srcloc, (const double2*)Q, nsrc, (const double2*)wavelet, c.slot_f,
                    c.slot_s, nb, c.q, c.err + 1, c.st);
+    // warm start: the caller's initial fields of this batch's pairs
+    if (U0) launch_copy_fields((const double2*)U0, c.u, c.slot_g, nb, c.ident, n, c.st);
     std::vector<SlotReport> rep;
-    st = solve_batch(c, 0, c.q, c.u, nb, rep);
+    st = solve_batch(c, 0, c.q, c.u, nb, rep, nullptr, U0 != nullptr);
     if (st == HELM_E_CUDA || st == HELM_E_TIMEOUT) return st;
     result = worst(result, st);
     for (auto& r : rep) result = worst(result, r.status);

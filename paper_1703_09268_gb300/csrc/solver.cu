@@ -509,9 +509,11 @@ static void jacobi(Ctx& c, const cplx<R>* in, Scale<R> ins, cplx<R>* out) {
   }
 }
 
-// Outer tolerance-driven solve in precision R of H x = b (b, x in R).
+// Outer tolerance-driven solve in precision R of H x = b (b, x in R), from
+// x = 0 or (warm) from the x given.
 template <typename R>
-static int outer_solve(Ctx& c, const cplx<R>* b, cplx<R>* x, double tol, KrylovOut* ko, bool final_resid) {
+static int outer_solve(Ctx& c, const cplx<R>* b, cplx<R>* x, double tol, KrylovOut* ko, bool final_resid,
+                       bool warm = false) {
   const helm_solve_opts& o = c.P->o;
   Hierarchy<R>& H = hier<R>(c);
   typename PrecT<R>::T pc;
@@ -523,7 +525,7 @@ static int outer_solve(Ctx& c, const cplx<R>* b, cplx<R>* x, double tol, KrylovO
     pc = [&c](const cplx<R>* i, Scale<R> s, cplx<R>* z) { jacobi<R>(c, i, s, z); };
     pp = &pc;
   }
-  return krylov<R>(c, H.inst[0], b, Scale<R>{}, x, true, o.max_cycles, tol, pp, ko, final_resid);
+  return krylov<R>(c, H.inst[0], b, Scale<R>{}, x, !warm, o.max_cycles, tol, pp, ko, final_resid);
 }
 
 template <typename R>
@@ -548,7 +550,7 @@ int precond_apply(Ctx& c, int dir, const void* x, void* z) {
 }
 
 int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep,
-                const std::vector<int>* only) {
+                const std::vector<int>* only, bool warm) {
   const helm_plan& P = *c.P;
   const helm_solve_opts& o = P.o;
   c.dir = dir;
@@ -571,16 +573,22 @@ int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vect
   const OpView<double> op64 = op_view<double>(c, 0, dir);
   norms<double>(c, q, Scale<double>{}, n, c.qn);
   if (!c.mixed) {
-    st = outer_solve<double>(c, q, u, o.tol, &ko, true);
+    st = outer_solve<double>(c, q, u, o.tol, &ko, true, warm);
     cudaMemcpyAsync(rn.data(), c.h64.inst[0].ks.rnorm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
     cudaMemcpyAsync(qn.data(), c.qn, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
     for (int a : solved) rep[a].refine = 1;
   } else {
     // FP64 iterative refinement around complex64 inner solves:
     //   r = q - H u (FP64), e = H^{-1}(r/||r||) (complex64), u += ||r|| e (FP64)
-    launch_zero<double>(u, c.act, c.na, n, c.st);
-    cudaMemcpyAsync(c.r64, q, sizeof(double2) * (size_t)nb * n, cudaMemcpyDeviceToDevice, c.st);
-    cudaMemcpyAsync(c.nrm, c.qn, sizeof(double) * nb, cudaMemcpyDeviceToDevice, c.st);
+    if (warm) {
+      Epi e0 = make_epi(c, EPI_NORM);
+      e0.out = c.nrm;
+      launch_stencil<double>(op64, c.slot_f, c.act, c.na, u, Scale<double>{}, q, Scale<double>{}, c.r64, c.st, &e0);
+    } else {
+      launch_zero<double>(u, c.act, c.na, n, c.st);
+      cudaMemcpyAsync(c.r64, q, sizeof(double2) * (size_t)nb * n, cudaMemcpyDeviceToDevice, c.st);
+      cudaMemcpyAsync(c.nrm, c.qn, sizeof(double) * nb, cudaMemcpyDeviceToDevice, c.st);
+    }
     for (int it = 0; it <= o.max_refine; ++it) {
       cudaMemcpyAsync(rn.data(), c.nrm, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);
       cudaMemcpyAsync(qn.data(), c.qn, sizeof(double) * c.B, cudaMemcpyDeviceToHost, c.st);

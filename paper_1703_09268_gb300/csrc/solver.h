@@ -118,8 +118,11 @@ void set_active(Ctx& c, const std::vector<int>& a);
 // Solve H u = q (dir 0) or H^H u = q (dir 1) for all slots of the batch, or
 // only for the slots listed in `only`; q and u are FP64 batch arrays.  Fills
 // rep[0..nb-1] (slots left out keep an empty report and their u untouched).
+// With `warm` the solves start from the u they are given (a slot whose
+// initial residual already meets the tolerance takes no iteration), else
+// from zero.
 int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep,
-                const std::vector<int>* only = nullptr);
+                const std::vector<int>* only = nullptr, bool warm = false);
 int sync_check(Ctx& c);
 // z = M^{-1} x for the active slots (the plan's preconditioner, the plan's
 // precision; dir 1 uses the adjoint operator H^H).

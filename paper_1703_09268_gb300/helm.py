@@ -82,7 +82,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.helm_workspace_size.argtypes = [P, I, I, I, I, ctypes.POINTER(S)]
     lib.helm_apply.argtypes = [P, P, D, I, I, P, P, I, P, S, P]
     lib.helm_precond_apply.argtypes = [P, P, D, I, P, P, I, P, S, P]
-    lib.helm_forward.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, S,
+    lib.helm_forward.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, I, P, P, P, P, S,
                                  ctypes.POINTER(HelmRhsReport), P]
     lib.helm_adjoint.argtypes = [P, P, ctypes.POINTER(D), I, P, I, P, I, P, P, S,
                                  ctypes.POINTER(HelmRhsReport), P]
@@ -332,8 +332,9 @@ def reports_to_list(rep):
 
 
 def helm_forward(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, wavelet=None, want_fields=True,
-                 want_data=True):
-    """Returns (U [nfreq, nsrc, n_comp] or None, D [nfreq, nsrc, nrec] or None, reports)."""
+                 want_data=True, U0=None):
+    """Returns (U [nfreq, nsrc, n_comp] or None, D [nfreq, nsrc, nrec] or None, reports).
+    U0 (complex128 [nfreq, nsrc, n_comp]) warm-starts the solves."""
     _dev(m_phys, torch.float64, "m_phys")
     _dev(src_idx, torch.int32, "src_idx")
     _dev(Q, torch.complex128, "Q")
@@ -345,13 +346,16 @@ def helm_forward(plan: Plan, m_phys, freqs_hz, src_idx, Q, rec_idx, wavelet=None
     nsrc = Q.shape[1]
     nrec = rec_idx.numel()
     dev = m_phys.device
+    if U0 is not None:
+        _dev(U0, torch.complex128, "U0")
+        _need(tuple(U0.shape) == (nfreq, nsrc, plan.n_comp), "U0 must be [nfreq, nsrc, n_comp]")
     U = torch.empty((nfreq, nsrc, plan.n_comp), dtype=torch.complex128, device=dev) if want_fields else None
     D = torch.empty((nfreq, nsrc, nrec), dtype=torch.complex128, device=dev) if want_data else None
     rep = _reports(nfreq * nsrc)
     ws, nb = plan.workspace(plan.workspace_size(CALL_FORWARD, nfreq, nsrc, nrec))
     code = lib().helm_forward(plan._h, _ptr(m_phys), _freqs(freqs_hz), nfreq, _ptr(src_idx), src_idx.numel(),
-                              _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(U), _ptr(D), ws, nb, rep,
-                              _stream(dev))
+                              _ptr(Q), nsrc, _ptr(wavelet), _ptr(rec_idx), nrec, _ptr(U0), _ptr(U), _ptr(D), ws, nb,
+                              rep, _stream(dev))
     _check(code, "helm_forward", allow_noconv=True)
     return U, D, reports_to_list(rep)
 

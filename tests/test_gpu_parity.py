@@ -218,3 +218,44 @@ def test_invalid_receiver_index_is_rejected(helm, wl3d):
         helm.helm_forward(plan, T(w["m0"].ravel(), torch.float64), w["freqs"], T(w["src"], torch.int32),
                           T(w["Q"], torch.complex128), T(bad, torch.int32))
     assert e.value.code == helm.HELM_E_INVAL
+
+
+@pytest.mark.parametrize("name", ["fp64-mlgmres", "mixed-mlgmres"])
+def test_3d_forward_warm_start(helm, wl3d, name):
+    """Warm starts (helm_forward's U0): a guess that already solves the system
+    to the tolerance takes no iteration and comes back unchanged; a perturbed
+    guess converges to the oracle's fields in fewer iterations than a cold
+    start; U0 may be the output array itself."""
+    w = wl3d
+    o = helm.default_opts(**OPTS[name], max_batch=4)
+    plan = helm.Plan(helm.make_grid(3, w["n"], w["h"], (6, 6, 6), 4500.0, levels=2), o, device=DEV)
+    args = (T(w["m0"].ravel(), torch.float64), w["freqs"], T(w["src"], torch.int32), T(w["Q"], torch.complex128),
+            T(w["rec"], torch.int32))
+    kw = dict(wavelet=T(w["wav"], torch.complex128))
+    U_ref, _ = O.forward(w["g"], w["m0"], w["freqs"], w["src"], w["Q"], w["rec"], wavelet=w["wav"])
+    tol = 1e-10 if OPTS[name]["precision"] == 0 else 1e-8
+    U, D, rep = helm.helm_forward(plan, *args, **kw)
+    cold = [r["iters"] for r in rep]
+    # converged guess: zero iterations, the guess itself returned
+    U2, D2, rep2 = helm.helm_forward(plan, *args, U0=U.clone(), **kw)
+    assert all(r["iters"] == 0 for r in rep2), rep2
+    assert torch.equal(U2, U) and torch.equal(D2, D)
+    assert all(r["status"] == 0 and r["rel_resid"] <= o.tol for r in rep2)
+    # a perturbed guess (about 1e-3 relative): fewer iterations, the oracle's fields
+    rng = np.random.default_rng(4)
+    noise = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    U0 = U + 1e-3 * U.abs().max() * T(noise, torch.complex128)
+    U3, _, rep3 = helm.helm_forward(plan, *args, U0=U0, **kw)
+    assert rel(U3.cpu().numpy(), U_ref) <= tol
+    assert sum(r["iters"] for r in rep3) < sum(cold), ([r["iters"] for r in rep3], cold)
+    # in place: U0 is the output array
+    U4 = U0.clone()
+    code = helm.lib().helm_forward(plan._h, helm._ptr(args[0]), helm._freqs(w["freqs"]), len(w["freqs"]),
+                                   helm._ptr(args[2]), args[2].numel(), helm._ptr(args[3]), args[3].shape[1],
+                                   helm._ptr(kw["wavelet"]), helm._ptr(args[4]), args[4].numel(), helm._ptr(U4),
+                                   helm._ptr(U4), None, *plan.workspace(plan.workspace_size(
+                                       helm.CALL_FORWARD, len(w["freqs"]), args[3].shape[1], args[4].numel())),
+                                   helm._reports(len(w["freqs"]) * args[3].shape[1]), helm._stream(DEV))
+    assert code == helm.HELM_OK
+    torch.cuda.synchronize()
+    assert rel(U4.cpu().numpy(), U_ref) <= tol
