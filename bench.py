@@ -53,7 +53,8 @@ def parse():
     p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     p.add_argument("--precond", default="mlgmres", choices=["mlgmres", "jacobi", "none"])
     p.add_argument("--levels", type=int, default=2)
-    p.add_argument("--tol", type=float, default=1e-9)
+    p.add_argument("--tol", type=float, default=None,
+                   help="FP64 relative residual of every solve (default 2e-10 on the 192^3 model, 1e-9 on the 64^3 one)")
     p.add_argument("--tol-inner", type=float, default=0.1)
     p.add_argument("--k-inner", type=int, default=0, help="outer FGMRES cycle length (0: 10 with ML-GMRES, else 30)")
     p.add_argument("--reorth", type=int, default=1)
@@ -67,6 +68,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3, help="steps timed end to end from host buffers")
     p.add_argument("--fp64-calls", type=int, default=5, help="timed calls of the FP64 per-source baseline")
     p.add_argument("--no-accuracy", action="store_true")
+    p.add_argument("--shape", type=int, default=None, help="apply mode: time only this stencil tile shape")
     p.add_argument("--no-fp64-baseline", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=None,
@@ -80,6 +82,8 @@ def parse():
                    help="step: the misfit+gradient benchmark; apply: the stencil alone (helm_apply on the "
                         "workload's 16 complex64 fields)")
     a = p.parse_args()
+    if a.tol is None:
+        a.tol = 2e-10 if a.workload == "multifreq192" and a.mode in ("step", "full") else 1e-9
     if a.cpu_seconds is None:
         a.cpu_seconds = 20.0 if a.workload == "multifreq192" else 15.0
     if a.smoother is None:
@@ -111,10 +115,17 @@ def run_apply(args):
         helm.profile_enable(False)
         return prof
 
-    for name_, dt, bpp in (("c64", torch.complex64, 16.0), ("c128", torch.complex128, 32.0)):
+    kinds = (("c64", torch.complex64, 16.0), ("c128", torch.complex128, 32.0))
+    if args.shape is not None:
+        kinds = kinds[:1]  # one forced complex64 shape (for a profiler capture)
+    for name_, dt, bpp in kinds:
         x = torch.randn(nf, plan.n_comp, dtype=dt, device=dev)
         y = torch.empty_like(x)
-        shapes = ([(v, sh) for v, sh in enumerate(helm.stencil_variants())] if name_ == "c64" else []) + [(-1, None)]
+        if args.shape is not None:
+            shapes = [(args.shape, helm.stencil_variants()[args.shape])]
+        else:
+            shapes = ([(v, sh) for v, sh in enumerate(helm.stencil_variants())] if name_ == "c64" else []) + \
+                [(-1, None)]
         for v, sh in shapes:
             helm.stencil_select(v)
             st = timed(x, y)["stencil_" + name_]
@@ -221,12 +232,12 @@ def make_workload(args, rank, world):
 
 
 # DRAM traffic of the single-precision stencil from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of k_stencil_plain<float, 0, 4>
-# on 16 fields of 85^3, `bench.py --mode apply`).  It scales with the points a
-# launch processes.  Set to None when the kernel changes until it is captured
-# again.
-STENCIL_TRAFFIC = dict(kernel="k_stencil_plain<float, 0, 4>", dram_bytes=81.184768e6 + 40.391424e6,
-                       algorithmic_bytes=16 * 614125 * 16 + 614125 * 4)
+# (dram__bytes_read.sum + dram__bytes_write.sum of k_stencil_plain<float, 0, 4,
+# 128, 32, 8> on the 8 fields of 213^3 of one step, `bench.py --mode apply
+# --shape 6`).  It scales with the points a launch processes.  Set to None when
+# the kernel changes until it is captured again.
+STENCIL_TRAFFIC = dict(kernel="k_stencil_plain<float, 0, 4, 128, 32, 8>", dram_bytes=739.457792e6 + 581.15968e6,
+                       algorithmic_bytes=8 * 9663597 * 16 + 9663597 * 4)
 
 
 def stencil_traffic(kernel_class, bytes_per_launch):

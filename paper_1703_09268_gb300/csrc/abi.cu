@@ -252,6 +252,7 @@ int helm_workspace_size(const helm_plan* P, int call, int nfreq, int nsrc, int n
 
 int helm_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, int precision,
                const void* x, void* y, int nrhs, void* ws, size_t ws_bytes, helm_stream_t stream) {
+  NvtxRange nvtx("helm_apply");
   if (!P || !m_phys || !x || !y || nrhs < 1 || !(freq_hz > 0.0) || !std::isfinite(freq_hz))
     return HELM_E_INVAL;
   if (precision != HELM_FP64 && precision != HELM_MIXED) return HELM_E_INVAL;
@@ -275,6 +276,7 @@ int helm_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, 
 
 int helm_precond_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, const void* x, void* z,
                        int nrhs, void* ws, size_t ws_bytes, helm_stream_t stream) {
+  NvtxRange nvtx("helm_precond_apply");
   if (!P || !m_phys || !x || !z || nrhs < 1 || !(freq_hz > 0.0) || !std::isfinite(freq_hz)) return HELM_E_INVAL;
   Ctx c;
   int st = bind(P, HELM_CALL_PRECOND, 1, nrhs, 0, ws, ws_bytes, stream, c);
@@ -312,6 +314,7 @@ int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int
                  const int32_t* src_idx, int n_srcloc, const void* Q, int nsrc, const void* wavelet,
                  const int32_t* rec_idx, int nrec, const void* U0, void* U_out, void* D_out, void* ws,
                  size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx("helm_forward");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || nrec < 0 || (nrec > 0 && !rec_idx)) return HELM_E_INVAL;
@@ -349,6 +352,7 @@ int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int
 int helm_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq,
                  const int32_t* rec_idx, int nrec, const void* R_in, int nsrc, void* V_out, void* ws,
                  size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx("helm_adjoint");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!rec_idx || nrec < 1 || !R_in || !V_out) return HELM_E_INVAL;
@@ -383,6 +387,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
                         const int32_t* rec_idx, int nrec, const void* d_obs, const uint8_t* mask,
                         double* f_out, double* g_out, void* ws, size_t ws_bytes, helm_rhs_report* reports,
                         helm_stream_t stream) {
+  NvtxRange nvtx("misfit_and_gradient");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out || !g_out)
@@ -481,6 +486,7 @@ static int linearised(int kind, helm_plan* P, const double* m_phys, const double
                       const int32_t* rec_idx, int nrec, const double* dm_phys, const void* dD_in,
                       const uint8_t* mask, void* dD_out, double* g_out, void* ws, size_t ws_bytes,
                       helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx(kind == 0 ? "helm_born" : kind == 1 ? "helm_born_adjoint" : kind == 2 ? "helm_gn_hessvec" : "helm_hessvec");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1) return HELM_E_INVAL;
@@ -599,6 +605,7 @@ int helm_misfit_and_gradient_25d(helm_plan* P, const double* m_phys, const doubl
                                  const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
                                  const void* d_obs, double* f_out, double* g_out, void* ws, size_t ws_bytes,
                                  helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx("helm_misfit_and_gradient_25d");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (P->g.dim != 2 || !ky || !ck || nk < 1 || !src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs ||
@@ -678,6 +685,7 @@ int helm_wri_misfit_and_gradient(helm_plan* P, const double* m_phys, const doubl
                                  const int32_t* rec_idx, int nrec, const void* d_obs, double lambda, double cg_tol,
                                  int cg_maxit, double* f_out, double* g_out, void* ws, size_t ws_bytes,
                                  helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx("helm_wri_misfit_and_gradient");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out || !g_out) return HELM_E_INVAL;
@@ -794,6 +802,7 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
                 int n_srcloc, const void* Q, int nsrc, const void* wavelet, const int32_t* rec_idx, int nrec,
                 const void* d_obs, const uint8_t* mask, double* f_out, void* R_out, void* U_out, int u_type,
                 void* ws, size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx("helm_misfit");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!src_idx || n_srcloc < 1 || !Q || !rec_idx || nrec < 1 || !d_obs || !f_out) return HELM_E_INVAL;
@@ -840,6 +849,7 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
 int helm_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, int nfreq, const int32_t* rec_idx,
                   int nrec, const void* R_in, int nsrc, const void* U_in, int u_type, const uint8_t* mask,
                   double* g_out, void* ws, size_t ws_bytes, helm_rhs_report* reports, helm_stream_t stream) {
+  NvtxRange nvtx("helm_gradient");
   int st = check_common(P, m_phys, freqs_hz, nfreq, nsrc);
   if (st != HELM_OK) return st;
   if (!rec_idx || nrec < 1 || !R_in || !U_in || !g_out) return HELM_E_INVAL;

@@ -551,6 +551,7 @@ int precond_apply(Ctx& c, int dir, const void* x, void* z) {
 
 int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep,
                 const std::vector<int>* only, bool warm) {
+  NvtxRange nvtx(dir ? "adjoint solves" : "forward solves");
   const helm_plan& P = *c.P;
   const helm_solve_opts& o = P.o;
   c.dir = dir;

@@ -1,12 +1,23 @@
 // Host-side solver orchestration and workspace layout (internal).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <functional>
 #include <vector>
 
 #include "common.cuh"
 
 namespace helm {
+
+// A named NVTX range for the lifetime of the object (calls and solves show up
+// as ranges in NVTX-aware profilers; without one attached it costs a branch).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Sub-allocates the caller's workspace; with base == nullptr it only sizes.
 struct Bump {

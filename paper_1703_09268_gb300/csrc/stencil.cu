@@ -73,8 +73,8 @@ k_stencil_plain(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss
   const C* Tz = T + 6 * G.Nmax;
   const int z0 = zc * ZR;
   const int z1 = min(z0 + ZR, G.K2);
-  if (threadIdx.x < 3 * ZR) {
-    const int k = threadIdx.x / ZR, zz = threadIdx.x % ZR;
+  for (int i = threadIdx.x; i < 3 * ZR; i += TPB) {
+    const int k = i / ZR, zz = i % ZR;
     stz[k][zz] = z0 + zz < G.K2 ? Tz[k * G.Nmax + z0 + zz] : mkc(R(0), R(0));
   }
   __syncthreads();
@@ -355,7 +355,8 @@ void stencil_red(dim3 grd, cudaStream_t st, const OpView<R>& op, const int* slot
 struct PlainShape {
   int tpb, zr, minb;
 };
-constexpr PlainShape kPlain[] = {{128, 16, 6}, {128, 16, 8}, {128, 32, 6}, {256, 16, 3}, {128, 8, 8}, {256, 8, 4}};
+constexpr PlainShape kPlain[] = {{128, 16, 6}, {128, 16, 8}, {128, 32, 6}, {256, 16, 3},
+                                 {128, 8, 8},  {256, 8, 4},  {128, 32, 8}, {64, 32, 16}};
 constexpr int kNumPlain = (int)(sizeof(kPlain) / sizeof(kPlain[0]));
 
 std::atomic<int> g_plain_forced{-1};  // >= 0: every plain apply uses this shape
@@ -394,6 +395,8 @@ void plain_variant(int v, cudaStream_t st, const OpView<R>& op, const int* slot_
     case 3: plain_go<R, RESID, PF, 256, 16, 3>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
     case 4: plain_go<R, RESID, PF, 128, 8, 8>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
     case 5: plain_go<R, RESID, PF, 256, 8, 4>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    case 6: plain_go<R, RESID, PF, 128, 32, 8>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
+    case 7: plain_go<R, RESID, PF, 64, 32, 16>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
     default: plain_go<R, RESID, PF, 128, 16, 6>(st, op, slot_f, act, na, x, xs, b, bs, y); break;
   }
 }
