@@ -158,17 +158,24 @@ def run_batch(args):
                                  tol=args.tol, tol_inner=args.tol_inner, k_so=kso, k_si=ksi, k_co=kco, k_ci=kci,
                                  max_batch=args.max_batch or 32)
         plan = helm.Plan(grid, opts, device=dev)
-        T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
         src, Q, rec = T(wl.src_idx, torch.int32), T(wl.Q, torch.complex128), T(wl.rec_idx, torch.int32)
-        # observed data: forward modelling in the true model (input generation, untimed)
-        _, d, _ = helm.helm_forward(plan, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
+        # observed data: forward modelling in the true model (input generation, untimed), complex64 inner
+        # solves refined in FP64 to 1e-11
+        p_obs = helm.Plan(grid, helm.default_opts(precision=helm.MIXED, tol=1e-11, k_so=kso, k_si=ksi, k_co=kco,
+                                                  k_ci=kci, max_batch=32), device=dev)
+        _, d, _ = helm.helm_forward(p_obs, T(wl.m_true.ravel(), torch.float64), wl.freqs_hz, src, Q, rec,
                                     want_fields=False)
+        p_obs.close()
+        del p_obs
+        torch.cuda.empty_cache()
         reqs.append(dict(plan=plan, m_phys=T(wl.m0.ravel(), torch.float64), freqs_hz=wl.freqs_hz, src_idx=src, Q=Q,
                          rec_idx=rec, d_obs=d))
     units = sum(len(w.freqs_hz) * w.nsrc for w in wls)
     out = dict(mode="batch", models=[w.name for w in wls], pairs=units, precision=args.precision, tol=args.tol)
-    for nw in (args.workers, 1):
-        for _ in range(max(1, args.warmup)):
+    # FP64 (the workload as stated) is ~10x slower: timed with the work queue only
+    for nw in ((args.workers,) if args.precision == "fp64" else (args.workers, 1)):
+        for _ in range(args.warmup):
             helm.misfit_and_gradient_batch(reqs, nworkers=nw)
         torch.cuda.synchronize()
         t0 = time.time()
@@ -177,7 +184,9 @@ def run_batch(args):
         torch.cuda.synchronize()
         dt = (time.time() - t0) / args.steps
         out[f"workers_{nw}"] = dict(value=round(units / dt, 3), unit=UNIT, s_per_step=round(dt, 3),
-                                    max_rel_resid=max(r["rel_resid"] for _, _, rep in res for r in rep))
+                                    max_rel_resid=max(r["rel_resid"] for _, _, rep in res for r in rep),
+                                    statuses=sorted({r["status"] for _, _, rep in res for r in rep}))
+    out["max_batch"] = args.max_batch or 32
     print(json.dumps(out), flush=True)
 
 

@@ -62,7 +62,9 @@ typedef enum {
   HELM_E_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
   HELM_E_NOCONV = -4,    /* some solve missed its tolerance (outputs written) */
   HELM_E_NONFINITE = -5, /* NaN/Inf met in a residual */
-  HELM_E_TIMEOUT = -6    /* a kernel gave up on a bounded wait for its bulk copies; outputs are void */
+  HELM_E_TIMEOUT = -6,   /* a kernel gave up on a bounded wait for its bulk copies; outputs are void */
+  HELM_E_BOUNDS = -7     /* debug build (HELM_DEBUG) only: a kernel wrote into the guard band after a
+                            workspace array, or a slot index was out of range; outputs are void */
 } helm_status;
 
 typedef enum { HELM_FP64 = 0, HELM_MIXED = 1 } helm_precision;
@@ -431,6 +433,20 @@ int helm_stencil_tuned(const helm_plan* plan, int level, int residual, int* vari
  * the wait completed (never expected); HELM_E_CUDA a launch or copy error.
  * Blocks the host for the duration of the wait. */
 int helm_check_bounded_wait(helm_stream_t stream);
+
+/* Debug build (libhelm_debug.so, compiled with HELM_DEBUG; no counterpart in
+ * the paper).  That build leaves a 256-byte guard band filled with 0xA5 after
+ * every array it lays out in a workspace, checks on the host that every slot
+ * index it hands to the kernels is in range, and ends every entry point by
+ * checking the bands: HELM_E_BOUNDS reports a write past the end of an array
+ * (workspace sizes grow by the bands).  helm_debug_guard_selftest arms the
+ * bands of an operator-apply workspace (sized by helm_workspace_size with
+ * HELM_CALL_APPLY, nfreq = nsrc = 1), checks them (HELM_OK expected), then
+ * changes one byte of the first band from the host and checks again:
+ * HELM_E_BOUNDS is the expected result.  Not exported by the release build. */
+#ifdef HELM_DEBUG
+int helm_debug_guard_selftest(helm_plan* plan, void* workspace, size_t ws_bytes, helm_stream_t stream);
+#endif
 
 /* Static description of a status code. */
 const char* helm_status_string(int status);

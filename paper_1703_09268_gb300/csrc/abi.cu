@@ -162,7 +162,7 @@ static int bind(helm_plan* P, int call, int nfreq, int nsrc, int nrec, void* ws,
   if (!aligned256(ws)) return HELM_E_INVAL;
   layout(*P, call, nfreq, nsrc, nrec, (char*)ws, &c);
   c.st = (cudaStream_t)stream;
-  return HELM_OK;
+  return arm_guards(c);
 }
 
 static int read_err(Ctx& c, int* h) {
@@ -271,7 +271,7 @@ int helm_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, 
     launch_stencil<float>(op_view<float>(c, 0, dir), c.slot_f, c.act, c.na, (const float2*)x,
                           Scale<float>{}, nullptr, Scale<float>{}, (float2*)y, c.st);
   }
-  return sync_check(c);
+  return final_check(c);
 }
 
 int helm_precond_apply(helm_plan* P, const double* m_phys, double freq_hz, int adjoint, const void* x, void* z,
@@ -292,7 +292,7 @@ int helm_precond_apply(helm_plan* P, const double* m_phys, double freq_hz, int a
     st = precond_apply(c, adjoint ? 1 : 0, (const char*)x + (size_t)start * n * esz, (char*)z + (size_t)start * n * esz);
     if (st != HELM_OK) return st;
   }
-  return HELM_OK;
+  return final_check(c);
 }
 
 static int check_common(helm_plan* P, const double* m_phys, const double* freqs, int nfreq, int nsrc) {
@@ -345,7 +345,7 @@ int helm_forward(helm_plan* P, const double* m_phys, const double* freqs_hz, int
     if (D_out) launch_receivers(*P, c.u, rec_idx, nrec, c.slot_g, nb, (double2*)D_out, nrec, c.st);
     fill_reports(reports, g, rep);
   }
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -378,7 +378,7 @@ int helm_adjoint(helm_plan* P, const double* m_phys, const double* freqs_hz, int
     launch_copy_fields(c.v, (double2*)V_out, c.ident, nb, c.slot_g, n, c.st);
     fill_reports(reports, g, rep);
   }
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -450,7 +450,7 @@ int misfit_and_gradient(helm_plan* P, const double* m_phys, const double* freqs_
     fill_reports(reports, g, rf);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -580,7 +580,7 @@ static int linearised(int kind, helm_plan* P, const double* m_phys, const double
     fill_reports(reports, g, rep);
   }
   if (kind != 0) launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -676,7 +676,7 @@ int helm_misfit_and_gradient_25d(helm_plan* P, const double* m_phys, const doubl
     fill_reports(reports, gl, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -778,7 +778,7 @@ int helm_wri_misfit_and_gradient(helm_plan* P, const double* m_phys, const doubl
     fill_reports(reports, g, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -842,7 +842,7 @@ int helm_misfit(helm_plan* P, const double* m_phys, const double* freqs_hz, int 
       launch_copy_fields(c.u, (double2*)U_out, c.ident, nb, c.slot_g, n, c.st);
     fill_reports(reports, g, rep);
   }
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
 
@@ -885,9 +885,25 @@ int helm_gradient(helm_plan* P, const double* m_phys, const double* freqs_hz, in
     fill_reports(reports, g, rep);
   }
   launch_extend_adjoint(*P, c.gcomp, g_out, c.st);
-  if (const int sc = sync_check(c); sc != HELM_OK) return sc;
+  if (const int sc = final_check(c); sc != HELM_OK) return sc;
   return result;
 }
+
+#ifdef HELM_DEBUG
+int helm_debug_guard_selftest(helm_plan* P, void* ws, size_t ws_bytes, helm_stream_t stream) {
+  if (!P) return HELM_E_INVAL;
+  Ctx c;
+  int st = bind(P, HELM_CALL_APPLY, 1, 1, 0, ws, ws_bytes, stream, c);
+  if (st != HELM_OK) return st;
+  if ((st = final_check(c)) != HELM_OK) return st;  // freshly armed guards are intact
+  if (c.guards.empty()) return HELM_E_CUDA;
+  // a stray one-byte write just past the first array, from the host API
+  const unsigned char stray = 0x5A;
+  if (cudaMemcpyAsync(c.ws_base + c.guards[0], &stray, 1, cudaMemcpyHostToDevice, c.st) != cudaSuccess)
+    return HELM_E_CUDA;
+  return final_check(c);
+}
+#endif
 
 const char* helm_status_string(int s) {
   switch (s) {
@@ -898,6 +914,7 @@ const char* helm_status_string(int s) {
     case HELM_E_NOCONV: return "solve did not reach its tolerance";
     case HELM_E_NONFINITE: return "non-finite residual";
     case HELM_E_TIMEOUT: return "device wait timed out";
+    case HELM_E_BOUNDS: return "debug build: write outside a workspace array or slot index out of range";
     default: return "unknown status";
   }
 }

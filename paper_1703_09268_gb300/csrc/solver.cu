@@ -84,11 +84,27 @@ static void layout_hierarchy(Bump& bp, const helm_plan& P, Hierarchy<R>& H, int 
   }
 }
 
+static size_t layout_body(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, Bump& bp, Ctx& C);
+
 size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char* base, Ctx* c) {
   Ctx local;
   Ctx& C = c ? *c : local;
   Bump bp;
   bp.base = base;
+  C.guards.clear();
+  bp.guards = &C.guards;
+  layout_body(P, call, nfreq, nsrc, nrec, bp, C);
+#ifdef HELM_DEBUG
+  // the device copy of the guard list (its own band is not in the list)
+  const size_t ng = C.guards.size();
+  C.guards_dev = bp.take<size_t>(ng > 0 ? ng : 1);
+  C.guards.resize(ng);
+#endif
+  C.ws_base = base;
+  return bp.off;
+}
+
+static size_t layout_body(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, Bump& bp, Ctx& C) {
   const int nrhs = nfreq * nsrc;
   int B = nrhs;
   if (call != HELM_CALL_APPLY && P.o.max_batch > 0 && P.o.max_batch < B) B = P.o.max_batch;
@@ -119,7 +135,7 @@ size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char*
   C.slot_g = bp.take<int>(B);
   C.act = bp.take<int>(B);
   C.ident = bp.take<int>(B);
-  C.err = bp.take<int>(4);
+  C.err = bp.take<int>(8);
   if (call == HELM_CALL_APPLY) return bp.off;
   // partial rows: at most max(RED_BLOCKS_MAX, B) rows of at most max(2(KMAX+1), Gram) values
   C.partial = bp.take<double>((size_t)std::max(RED_BLOCKS_MAX, B) *
@@ -223,7 +239,55 @@ int sync_check(Ctx& c) {
   return HELM_OK;
 }
 
+#ifdef HELM_DEBUG
+// One block per guard band: any byte that is not the guard pattern marks err[2].
+__global__ void k_check_guards(const unsigned char* __restrict__ base, const size_t* __restrict__ guards,
+                               int* __restrict__ bad) {
+  const unsigned char* g = base + guards[blockIdx.x];
+  for (unsigned i = threadIdx.x; i < kGuardBytes; i += blockDim.x)
+    if (g[i] != kGuardByte) atomicOr(bad, 1);
+}
+#endif
+
+int arm_guards(Ctx& c) {
+#ifdef HELM_DEBUG
+  if (!c.ws_base) return HELM_OK;
+  for (size_t off : c.guards) cudaMemsetAsync(c.ws_base + off, kGuardByte, kGuardBytes, c.st);
+  if (!c.guards.empty())
+    cudaMemcpyAsync(c.guards_dev, c.guards.data(), sizeof(size_t) * c.guards.size(), cudaMemcpyHostToDevice, c.st);
+  c.host_fault = false;
+  return cudaGetLastError() == cudaSuccess ? HELM_OK : HELM_E_CUDA;
+#else
+  (void)c;
+  return HELM_OK;
+#endif
+}
+
+int final_check(Ctx& c) {
+  int st = sync_check(c);
+  if (st != HELM_OK) return st;
+#ifdef HELM_DEBUG
+  if (c.ws_base && !c.guards.empty()) {
+    cudaMemsetAsync(c.err + 2, 0, sizeof(int), c.st);
+    k_check_guards<<<(unsigned)c.guards.size(), 64, 0, c.st>>>((const unsigned char*)c.ws_base, c.guards_dev,
+                                                              c.err + 2);
+    count_launch();
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, c.err + 2, sizeof(int), cudaMemcpyDeviceToHost, c.st) != cudaSuccess ||
+        cudaStreamSynchronize(c.st) != cudaSuccess)
+      return HELM_E_CUDA;
+    if (bad) return HELM_E_BOUNDS;
+  }
+  if (c.host_fault) return HELM_E_BOUNDS;
+#endif
+  return HELM_OK;
+}
+
 void set_active(Ctx& c, const std::vector<int>& a) {
+#ifdef HELM_DEBUG
+  for (int s : a)
+    if (s < 0 || s >= c.B) c.host_fault = true;
+#endif
   c.act_h = a;
   c.na = (int)a.size();
   if (c.na > 0)
@@ -246,7 +310,7 @@ int setup_operator(Ctx& c, const double* m_phys, const double* freqs_hz) {
   std::vector<int> id(c.B);
   for (int i = 0; i < c.B; ++i) id[i] = i;
   cudaMemcpyAsync(c.ident, id.data(), sizeof(int) * c.B, cudaMemcpyHostToDevice, c.st);
-  cudaMemsetAsync(c.err, 0, 4 * sizeof(int), c.st);
+  cudaMemsetAsync(c.err, 0, 8 * sizeof(int), c.st);
   if (c.counter) cudaMemsetAsync(c.counter, 0, sizeof(unsigned) * c.B, c.st);
   launch_extend(P, m_phys, c.m64[0], c.m32[0], c.st);
   for (int l = 1; l < L; ++l) {
@@ -261,6 +325,11 @@ int setup_operator(Ctx& c, const double* m_phys, const double* freqs_hz) {
 
 int set_batch_fs(Ctx& c, const std::vector<int>& g, const std::vector<int>& f, const std::vector<int>& s) {
   const int nb = (int)g.size();
+#ifdef HELM_DEBUG
+  if (nb > c.B) c.host_fault = true;
+  for (int a = 0; a < nb; ++a)
+    if (f[a] < 0 || f[a] >= c.nfreq || s[a] < 0 || s[a] >= c.nsrc) c.host_fault = true;
+#endif
   cudaMemcpyAsync(c.slot_f, f.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.st);
   cudaMemcpyAsync(c.slot_s, s.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.st);
   cudaMemcpyAsync(c.slot_g, g.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c.st);
@@ -272,6 +341,11 @@ int set_batch_fs(Ctx& c, const std::vector<int>& g, const std::vector<int>& f, c
 
 int set_batch(Ctx& c, const std::vector<int>& g) {
   const int nb = (int)g.size();
+#ifdef HELM_DEBUG
+  if (nb > c.B) c.host_fault = true;
+  for (int v : g)
+    if (v < 0 || v >= c.nfreq * c.nsrc) c.host_fault = true;
+#endif
   std::vector<int> f(nb), s(nb);
   for (int a = 0; a < nb; ++a) {
     f[a] = g[a] / c.nsrc;

@@ -19,14 +19,26 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Bytes of the guard band a debug build (HELM_DEBUG) leaves after every
+// workspace array; bind() fills them with kGuardByte and the end of each call
+// checks that no kernel wrote into one.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
 // Sub-allocates the caller's workspace; with base == nullptr it only sizes.
 struct Bump {
   char* base = nullptr;
   size_t off = 0;
+  std::vector<size_t>* guards = nullptr;  // debug build: offsets of the guard bands
   template <typename T> T* take(size_t count) {
     off = (off + 255) & ~(size_t)255;
     T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
     off += count * sizeof(T);
+#ifdef HELM_DEBUG
+    off = (off + 255) & ~(size_t)255;
+    if (guards) guards->push_back(off);
+    off += kGuardBytes;
+#endif
     return p;
   }
 };
@@ -107,6 +119,11 @@ struct Ctx {
   // host state
   std::vector<int> act_h;
   int na = 0;
+  // debug build: workspace base, guard-band offsets (host list and device copy), host-side index faults
+  char* ws_base = nullptr;
+  std::vector<size_t> guards;
+  size_t* guards_dev = nullptr;
+  bool host_fault = false;
 };
 
 size_t layout(const helm_plan& P, int call, int nfreq, int nsrc, int nrec, char* base, Ctx* c);
@@ -135,6 +152,12 @@ void set_active(Ctx& c, const std::vector<int>& a);
 int solve_batch(Ctx& c, int dir, const double2* q, double2* u, int nb, std::vector<SlotReport>& rep,
                 const std::vector<int>* only = nullptr, bool warm = false);
 int sync_check(Ctx& c);
+// sync_check, then (debug build) the guard bands and host-side index checks:
+// HELM_E_BOUNDS when a kernel wrote past the end of a workspace array or a
+// slot index was out of range.  Called at the end of every entry point.
+int final_check(Ctx& c);
+// Debug build: write the guard pattern and the guard list after layout().
+int arm_guards(Ctx& c);
 // z = M^{-1} x for the active slots (the plan's preconditioner, the plan's
 // precision; dir 1 uses the adjoint operator H^H).
 int precond_apply(Ctx& c, int dir, const void* x, void* z);

@@ -15,10 +15,12 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhelm.so")
+# HELM_LIBRARY=debug selects the bounds-checking build (libhelm_debug.so)
+LIB_PATH = os.path.join(_HERE, "libhelm_debug.so" if os.environ.get("HELM_LIBRARY") == "debug" else "libhelm.so")
 
 HELM_OK, HELM_E_INVAL, HELM_E_NOMEM, HELM_E_CUDA, HELM_E_NOCONV, HELM_E_NONFINITE, HELM_E_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6
+HELM_E_BOUNDS = -7  # debug build only
 FP64, MIXED = 0, 1
 FIELD_C128, FIELD_C64 = 0, 1
 PRECOND_NONE, PRECOND_JACOBI, PRECOND_MLGMRES = 0, 1, 2

@@ -24,6 +24,7 @@ def helm():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "helm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#ifdef HELM_DEBUG.*?#endif", "", src, flags=re.S)  # declared for the debug build only
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", src, flags=re.M))
                   - {"if", "defined"})
 
@@ -105,7 +106,7 @@ def test_workspace_sizes(helm):
 
 def test_status_strings(helm):
     L = helm.lib()
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert L.helm_status_string(code)
     assert L.helm_status_string(123) == b"unknown status"
 
@@ -186,3 +187,34 @@ def test_stored_field_type_is_checked_before_any_device_work(helm):
                              fake, 1 << 20, rep, None) == helm.HELM_E_INVAL
         assert L.helm_gradient(p3._h, fake, fr, 1, fake, 1, fake, 1, fake, bad, None, fake, fake, 1 << 20, rep,
                                None) == helm.HELM_E_INVAL
+
+
+def test_debug_build_exports_the_same_calls_and_its_self_test(helm):
+    """libhelm_debug.so (HELM_DEBUG) exports every call of the release library
+    plus helm_debug_guard_selftest, and its workspaces are larger by the guard
+    bands; the release library does not export the self-test."""
+    from paper_1703_09268_gb300 import build
+    if not os.path.exists(build.LIB_DEBUG):
+        build.build(variants=("debug",))
+    dbg = ctypes.CDLL(build.LIB_DEBUG)
+    for name in declared_functions():
+        assert hasattr(dbg, name), name
+    assert hasattr(dbg, "helm_debug_guard_selftest")
+    assert not hasattr(ctypes.CDLL(LIB), "helm_debug_guard_selftest")
+    P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    sizes = []
+    for lib in (ctypes.CDLL(LIB), dbg):
+        lib.helm_plan_create.argtypes = [ctypes.POINTER(helm.HelmGrid), ctypes.POINTER(helm.HelmSolveOpts),
+                                         ctypes.POINTER(P)]
+        lib.helm_workspace_size.argtypes = [P, I, I, I, I, ctypes.POINTER(S)]
+        lib.helm_plan_destroy.argtypes = [P]
+        lib.helm_plan_destroy.restype = None
+        g = helm.make_grid(3, (16, 16, 16), 25.0, (4, 4, 4), 3000.0, levels=2)
+        o = helm.default_opts()
+        h = P()
+        assert lib.helm_plan_create(ctypes.byref(g), ctypes.byref(o), ctypes.byref(h)) == 0
+        b = S()
+        assert lib.helm_workspace_size(h, helm.CALL_MISFIT_GRAD, 1, 4, 16, ctypes.byref(b)) == 0
+        sizes.append(b.value)
+        lib.helm_plan_destroy(h)
+    assert sizes[1] > sizes[0]
