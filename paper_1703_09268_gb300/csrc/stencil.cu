@@ -168,11 +168,16 @@ __global__ void __launch_bounds__(STPB)
 k_stencil(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, const cplx<R>* __restrict__ b,
           const R* __restrict__ bs, int bss, cplx<R>* __restrict__ y, const cplx<R>* __restrict__ tab,
           const R* __restrict__ m, const R* __restrict__ w2, const int* __restrict__ slot_f,
-          const int* __restrict__ act, TileGeom G, const cplx<R>* __restrict__ V, size_t vstride, int nv, Epi e) {
+          const int* __restrict__ act, int na, TileGeom G, const cplx<R>* __restrict__ V, size_t vstride, int nv,
+          Epi e) {
   using C = cplx<R>;
   constexpr int KM = RED > 0 ? RED : 1;
   constexpr int NVAL = RED > 0 ? 2 * RED : 1;
-  const int a = blockIdx.y;
+  // 1D grid, slots fastest: block j of every slot works on the same tiles at the same time, so the
+  // tiles of m are shared through L2; nb blocks per slot, each with its own partial row
+  const int a = (int)(blockIdx.x % (unsigned)na);
+  const int jb = (int)(blockIdx.x / (unsigned)na);
+  const int nb = (int)(gridDim.x / (unsigned)na);
   const int s = act[a];
   const int f = slot_f[s];
   const C* T = tab + (size_t)f * 9 * G.Nmax;
@@ -190,7 +195,7 @@ k_stencil(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, cons
 #pragma unroll
   for (int k = 0; k < NVAL; ++k) acc[k] = R(0);
   const int planei = G.K0 * G.K1;
-  for (int tile = blockIdx.x; tile < G.ntiles; tile += gridDim.x) {
+  for (int tile = jb; tile < G.ntiles; tile += nb) {
     const int seg = tile % G.nseg;
     const int zc = tile / G.nseg;
     const int p2 = seg * STPB + threadIdx.x;
@@ -264,8 +269,8 @@ k_stencil(const cplx<R>* __restrict__ x, const R* __restrict__ xs, int xss, cons
   }
   if (RED == 0) return;
   const int nvals = RED > 0 ? 2 * nv : 1;
-  block_partial_row<R, NVAL, STPB / 32>(acc, nvals, e.partial + ((size_t)a * gridDim.x + blockIdx.x) * nvals);
-  epi_arrive<R>(e, a, s, gridDim.x, nvals);
+  block_partial_row<R, NVAL, STPB / 32>(acc, nvals, e.partial + ((size_t)a * nb + jb) * nvals);
+  epi_arrive<R>(e, a, s, nb, nvals);
 }
 
 // Diagonal of H at p: sum of the three cd tables and w^2 m.
@@ -327,8 +332,9 @@ template <typename R, bool RESID, int RED>
 void stencil_go(dim3 grd, cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act,
                 const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y, const TileGeom& G,
                 const cplx<R>* V, size_t vstride, int nv, const Epi& e) {
-  k_stencil<R, RESID, RED><<<grd, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
-                                                          op.w2, slot_f, act, G, V, vstride, nv, e);
+  // grd = (blocks per slot, slots): launched as one dimension with the slots fastest
+  k_stencil<R, RESID, RED><<<grd.x * grd.y, STPB, 0, st>>>(x, xs.p, xs.stride, b, bs.p, bs.stride, y, op.tab, op.m,
+                                                            op.w2, slot_f, act, (int)grd.y, G, V, vstride, nv, e);
 }
 
 template <typename R, bool RESID>
