@@ -895,6 +895,7 @@ int helm_debug_guard_selftest(helm_plan* P, void* ws, size_t ws_bytes, helm_stre
   Ctx c;
   int st = bind(P, HELM_CALL_APPLY, 1, 1, 0, ws, ws_bytes, stream, c);
   if (st != HELM_OK) return st;
+  cudaMemsetAsync(c.err, 0, 8 * sizeof(int), c.st);  // no operator set-up here to clear the counters
   if ((st = final_check(c)) != HELM_OK) return st;  // freshly armed guards are intact
   if (c.guards.empty()) return HELM_E_CUDA;
   // a stray one-byte write just past the first array, from the host API
