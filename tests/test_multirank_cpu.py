@@ -132,3 +132,23 @@ def test_two_rank_hessian_products_equal_single_rank(tmp_path):
     n = gn.size
     assert np.allclose(got[:n], gn, rtol=1e-12, atol=1e-12 * np.abs(gn).max())
     assert np.allclose(got[n:], hv, rtol=1e-12, atol=1e-12 * np.abs(hv).max())
+
+
+def test_bench_step_sources_partition_the_multifrequency_workload():
+    """bench.py's rank-r step takes its own sources of the 192^3 recipe (same
+    8 x 16 source grid at any size): distinct across ranks, the centre source
+    first on rank 0, and each source's point (node index, unit weight) kept."""
+    import bench
+    from paper_1703_09268_gb300 import synth
+    wl = synth.workload_3d_multifreq(n=32)
+    s0 = synth.centre_source(wl)
+    nx, ny, _ = wl.n
+    loc = wl.src_idx[s0]
+    assert abs(loc % nx - (nx - 1) / 2) <= nx / 8 and abs((loc // nx) % ny - (ny - 1) / 2) <= ny / 8
+    for world in (1, 2, 4, 8):
+        for k in (1, 2):
+            cols = [c for r in range(world) for c in bench.step_columns(wl, r, k)]
+            assert len(set(cols)) == world * k and cols[0] == s0
+    src, Q = synth.source_subset(wl, [s0, (s0 + 1) % wl.nsrc])
+    assert list(src) == [wl.src_idx[s0], wl.src_idx[(s0 + 1) % wl.nsrc]]
+    assert np.array_equal(Q, np.eye(2))
