@@ -152,12 +152,14 @@ struct Epi;  // fused reduction + per-slot epilogue (reduce.cuh)
 
 // y = bs*b - xs*H x   (b == nullptr: y = xs*H x), for the active slots.  With an
 // epilogue the kernel also reduces y: the norm (EPI_NORM / EPI_START) or the
-// dots with basis vectors V_0..V_{nv-1} (EPI_DOTS).
+// dots with basis vectors V_0..V_{nv-1} (EPI_DOTS).  The plain apply picks
+// its tile shape per grid, timing the shapes on first use unless may_tune is
+// false (then a grid not tuned yet takes the first shape).
 template <typename R>
 void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int na,
                     const cplx<R>* x, Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y,
                     cudaStream_t st, const Epi* epi = nullptr, const cplx<R>* V = nullptr,
-                    size_t vstride = 0, int nv = 0);
+                    size_t vstride = 0, int nv = 0, bool may_tune = true);
 
 // Damped Jacobi: z = z + omega D^{-1}(bs*b - H z) (first sweep with z = 0 gives omega D^{-1} bs*b).
 template <typename R>

@@ -70,12 +70,14 @@ extern "C" int helm_apply_noalloc(helm_plan* P, const double* m_phys, double fre
   for (int i = 0; i < nrhs; ++i) g[i] = i;
   if ((st = set_batch(c, g)) != HELM_OK) return st;
   const int dir = adjoint ? 1 : 0;
+  // no shape tuning here (it would create timing events): a grid tuned by an earlier call keeps its
+  // shape, any other takes the first one -- the results are the same either way
   if (precision == HELM_FP64) {
     launch_stencil<double>(op_view<double>(c, 0, dir), c.slot_f, c.act, c.na, (const double2*)x, Scale<double>{},
-                           nullptr, Scale<double>{}, (double2*)y, c.st);
+                           nullptr, Scale<double>{}, (double2*)y, c.st, nullptr, nullptr, 0, 0, false);
   } else {
     launch_stencil<float>(op_view<float>(c, 0, dir), c.slot_f, c.act, c.na, (const float2*)x, Scale<float>{},
-                          nullptr, Scale<float>{}, (float2*)y, c.st);
+                          nullptr, Scale<float>{}, (float2*)y, c.st, nullptr, nullptr, 0, 0, false);
   }
   return sync_check(c);
 }

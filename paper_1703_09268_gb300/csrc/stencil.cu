@@ -414,7 +414,7 @@ void plain_variant(int v, cudaStream_t st, const OpView<R>& op, const int* slot_
 // three timed launches per shape; it synchronises the stream once per grid.
 template <typename R, bool RESID, int PF>
 int plain_choose(cudaStream_t st, const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* x,
-                 Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y) {
+                 Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y, bool may_tune) {
   const int forced = g_plain_forced.load();
   if (forced >= 0) return forced;
   if (sizeof(R) == 8 || op.n < PROF_COARSE_N) return 0;  // FP64, or grids that sit in L2: no tuning
@@ -422,6 +422,7 @@ int plain_choose(cudaStream_t st, const OpView<R>& op, const int* slot_f, const 
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_plain_choice.find(key);
   if (it != g_plain_choice.end()) return it->second.variant;
+  if (!may_tune) return 0;  // the caller may not create the timing events: the first shape
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -456,7 +457,7 @@ int plain_choose(cudaStream_t st, const OpView<R>& op, const int* slot_f, const 
 template <typename R>
 void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int na, const cplx<R>* x,
                     Scale<R> xs, const cplx<R>* b, Scale<R> bs, cplx<R>* y, cudaStream_t st, const Epi* epi,
-                    const cplx<R>* V, size_t vstride, int nv) {
+                    const cplx<R>* V, size_t vstride, int nv, bool may_tune) {
   if (na <= 0) return;
   Epi e = epi ? *epi : Epi{};
   double by = (double)na * op.n * (b ? 3 : 2) * sizeof(cplx<R>) + (double)op.n * sizeof(R);
@@ -466,10 +467,10 @@ void launch_stencil(const OpView<R>& op, const int* slot_f, const int* act, int 
     // grids that do not sit in L2 anyway.  The shape is chosen (tuned on first use) outside the timed scope.
     const bool pf = sizeof(R) == 4 && ((uintptr_t)x & 15) == 0 && op.n >= PROF_COARSE_N;
     int v;
-    if (b && pf) v = plain_choose<R, true, 4>(st, op, slot_f, act, na, x, xs, b, bs, y);
-    else if (b) v = plain_choose<R, true, 0>(st, op, slot_f, act, na, x, xs, b, bs, y);
-    else if (pf) v = plain_choose<R, false, 4>(st, op, slot_f, act, na, x, xs, b, bs, y);
-    else v = plain_choose<R, false, 0>(st, op, slot_f, act, na, x, xs, b, bs, y);
+    if (b && pf) v = plain_choose<R, true, 4>(st, op, slot_f, act, na, x, xs, b, bs, y, may_tune);
+    else if (b) v = plain_choose<R, true, 0>(st, op, slot_f, act, na, x, xs, b, bs, y, may_tune);
+    else if (pf) v = plain_choose<R, false, 4>(st, op, slot_f, act, na, x, xs, b, bs, y, may_tune);
+    else v = plain_choose<R, false, 0>(st, op, slot_f, act, na, x, xs, b, bs, y, may_tune);
     ProfScope ps(prof_stencil_class<R>(op.n), by, st);
     if (b && pf) plain_variant<R, true, 4>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
     else if (b) plain_variant<R, true, 0>(v, st, op, slot_f, act, na, x, xs, b, bs, y);
@@ -526,7 +527,7 @@ void launch_jacobi_update(const OpView<R>& op, const int* slot_f, const int* act
 #define INST(R)                                                                                                 \
   template void launch_stencil<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*, Scale<R>,      \
                                   const cplx<R>*, Scale<R>, cplx<R>*, cudaStream_t, const Epi*, const cplx<R>*, \
-                                  size_t, int);                                                                 \
+                                  size_t, int, bool);                                                           \
   template void launch_jacobi_first<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*, Scale<R>, \
                                        R, cplx<R>*, cudaStream_t);                                              \
   template void launch_jacobi_update<R>(const OpView<R>&, const int*, const int*, int, const cplx<R>*, R,        \
