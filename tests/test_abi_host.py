@@ -218,3 +218,22 @@ def test_debug_build_exports_the_same_calls_and_its_self_test(helm):
         sizes.append(b.value)
         lib.helm_plan_destroy(h)
     assert sizes[1] > sizes[0]
+
+
+def test_stencil_shape_calls_on_the_host(helm):
+    """The tile-shape calls need no device: the shape list, the range check of
+    a forced shape, going back to tuning, and 'not tuned yet' for a fresh grid."""
+    shapes = helm.stencil_variants()
+    assert len(shapes) >= 2
+    assert shapes[0] == dict(threads=128, zplanes=16, min_blocks=6)
+    for sh in shapes:
+        assert sh["threads"] in (64, 128, 256) and sh["zplanes"] in (8, 16, 32) and sh["min_blocks"] >= 1
+        assert sh["threads"] * sh["min_blocks"] <= 2048  # fits the SM's thread slots
+    L = helm.lib()
+    assert L.helm_stencil_select(len(shapes)) == helm.HELM_E_INVAL
+    assert L.helm_stencil_select(-2) == helm.HELM_E_INVAL
+    assert L.helm_stencil_variant_info(len(shapes), None, None, None) == helm.HELM_E_INVAL
+    assert L.helm_stencil_select(1) == helm.HELM_OK
+    assert L.helm_stencil_select(-1) == helm.HELM_OK
+    p = helm.Plan(helm.make_grid(3, (9, 7, 5), 25.0, (2, 2, 2), 3000.0), helm.default_opts(precond=0), device="cpu")
+    assert helm.stencil_tuned(p) is None
